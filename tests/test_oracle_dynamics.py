@@ -1,0 +1,407 @@
+"""Pins of the oracle's time step against special cases, invariants and exact flow solutions
+(no GPU).  Each test names the property of the paper or of the mathematics it checks."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1704_07559_gb300 import inputs as I
+
+TAU = 0.6
+S19 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / TAU, 1.4, 1 / TAU, 1.4, 1 / TAU, 1 / TAU, 1 / TAU, 1.98, 1.98, 1.98]
+S9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / TAU, 1 / TAU]
+PER = [O.PERIODIC] * 6
+CHANNEL = [O.PERIODIC, O.PERIODIC, O.WALL, O.WALL, O.PERIODIC, O.PERIODIC]
+
+
+def rates(q, tau=TAU):
+    s = list(S19 if q == 19 else S9)
+    for k in ((9, 11, 13, 14, 15) if q == 19 else (7, 8)):
+        s[k] = 1.0 / tau
+    return s
+
+
+def strain_from_grad(q, g):
+    """Symmetric part of a velocity gradient in the oracle's component order."""
+    if q == 19:
+        return np.stack([g[0], g[4], g[8], 0.5 * (g[1] + g[3]), 0.5 * (g[5] + g[7]), 0.5 * (g[2] + g[6])])
+    return np.stack([g[0], g[3], 0.5 * (g[1] + g[2])])
+
+
+# ------------------------------------------------------------------------------------------------
+# special cases that reduce to textbook routines
+
+
+@pytest.mark.parametrize("q", [19, 9])
+def test_srt_special_case_is_bgk(q):
+    """With every rate 1/tau, the MRT collision is the BGK collision (eq. (ChaiS_srt) context):
+    f* = f - (f - f_eq)/tau + (1 - 1/(2 tau)) Fbar, and Chai's S is the LBGK formula
+    S = -sum c c (f - f_eq + Fbar/2) / (2 rho0 cs2 tau)."""
+    c, w, T, Ti, opp = O.tables(q)
+    d = 3 if q == 19 else 2
+    rng = np.random.default_rng(q)
+    tau = 0.77
+    p = O.make_params(q, [1.0 / tau] * q, formula=O.CHAI)
+    for _ in range(20):
+        f = w * (1 + rng.normal(scale=0.01)) - w + rng.normal(scale=1e-3, size=q)
+        F = np.zeros(3)
+        F[:d] = rng.normal(scale=1e-4, size=d)
+        fout, S, _, _ = O.collide(p, f, F)
+        drho = f.sum()
+        j = c.T @ f + 0.5 * F
+        fe = O.feq(q, drho, j)
+        Fb = O.force_bar(q, j, F)
+        bgk = f - (f - fe) / tau + (1 - 0.5 / tau) * Fb
+        assert np.abs(fout - bgk).max() < 1e-16
+        cc = c[:, :d].astype(float)
+        P = np.einsum("i,ia,ib->ab", f - fe + 0.5 * Fb, cc, cc)
+        Sl = -P / (2 * tau / 3)
+        want = [Sl[0, 0], Sl[1, 1], Sl[2, 2], Sl[0, 1], Sl[1, 2], Sl[0, 2]] if q == 19 else [Sl[0, 0], Sl[1, 1],
+                                                                                              Sl[0, 1]]
+        assert np.abs(S - np.array(want)).max() < 1e-16
+
+
+@pytest.mark.parametrize("q,dims", [(19, (5, 4, 3)), (9, (7, 5, 1))])
+def test_zero_rates_is_pure_streaming(q, dims):
+    """With all rates zero and no force the step is free streaming: f_i(x + c_i) = f_i(x), a
+    periodic shift of each population array (numpy roll), up to the rounding of T^-1 T."""
+    c, w, T, Ti, opp = O.tables(q)
+    p = O.make_params(q, [0.0] * q)
+    G = O.Grid(p, *dims)
+    f = I.random_populations(q, G.shape, seed=1)
+    fn, _ = G.step(f)
+    for i in range(q):
+        want = np.roll(f[i], shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2))
+        assert np.abs(fn[i] - want).max() < 1e-15 * np.abs(f).max()
+
+
+def test_bounce_back_with_zero_rates_is_a_permutation():
+    """Halfway bounce-back with zero rates permutes the populations: the multiset of values is
+    unchanged (up to the rounding of T^-1 T)."""
+    q = 19
+    p = O.make_params(q, [0.0] * q, bc=[O.WALL] * 6)
+    G = O.Grid(p, 4, 3, 5)
+    f = I.random_populations(q, G.shape, seed=2)
+    fn, _ = G.step(f)
+    assert np.abs(np.sort(fn.ravel()) - np.sort(f.ravel())).max() < 1e-15 * np.abs(f).max()
+
+
+# ------------------------------------------------------------------------------------------------
+# invariants
+
+
+@pytest.mark.parametrize("q,formula,closure", [(19, O.YU, O.NEWTON), (19, O.CHAI, O.SMAG), (9, O.CHAI, O.POWERLAW),
+                                               (9, O.YU, O.NEWTON)])
+def test_conservation_periodic(q, formula, closure):
+    """Mass and momentum are collision invariants (s_0 = s_3 = s_5 = s_7 = 0) and periodic
+    streaming permutes populations: the global sums stay fixed to rounding."""
+    dims = (6, 5, 4) if q == 19 else (9, 7, 1)
+    p = O.make_params(q, rates(q), formula=formula, closure=closure, smag_cs=0.17, pl_n=0.6, pl_k=0.01)
+    G = O.Grid(p, *dims)
+    c, w, T, Ti, opp = O.tables(q)
+    f = I.random_populations(q, G.shape, scale=2e-3, seed=3)
+    s0 = G.sums(f)
+    for _ in range(5):
+        f, _ = G.step(f)
+    s1 = G.sums(f)
+    assert np.abs(s1 - s0).max() < 1e-13 * G.N * np.abs(f).max()
+
+
+@pytest.mark.parametrize("q", [19, 9])
+def test_uniform_force_momentum_growth(q):
+    """With a uniform body force F each step adds F to the momentum of every node:
+    sum j grows by N F per step, mass is unchanged."""
+    d = 3 if q == 19 else 2
+    dims = (5, 4, 3) if q == 19 else (6, 5, 1)
+    F = np.array([2e-5, -1e-5, 3e-5])[:d]
+    p = O.make_params(q, rates(q))
+    G = O.Grid(p, *dims)
+    f = I.random_populations(q, G.shape, scale=2e-3, seed=4)
+    s0 = G.sums(f, force=F)
+    for n in range(1, 4):
+        f, _ = G.step(f, force=F)
+        s = G.sums(f, force=F)
+        assert abs(s[0] - s0[0]) < 1e-15 * G.N
+        assert np.abs(s[1:] - (s0[1:] + n * G.N * F)).max() < 1e-15 * G.N
+
+
+@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("formula", [O.YU, O.CHAI])
+def test_uniform_flow_under_force_has_zero_strain(q, formula):
+    """A spatially uniform flow accelerated by a uniform force has no velocity gradient, so the
+    strain rate is zero at every step.  This fixes the half-force shift of both formulas:
+    without it S would be of order u F (~1e-7 here)."""
+    d = 3 if q == 19 else 2
+    dims = (3, 2, 2) if q == 19 else (3, 2, 1)
+    F = np.array([1e-5, -2e-5, 3e-5])[:d]
+    p = O.make_params(q, rates(q), formula=formula)
+    G = O.Grid(p, *dims)
+    shape = G.shape
+    u = np.zeros((d,) + shape)
+    u[0], u[1] = 0.02, -0.01
+    if d == 3:
+        u[2] = 0.005
+    f = G.init(np.full(shape, 1e-3), u, force=F)
+    for _ in range(10):
+        f, out = G.step(f, force=F, want=("S", "u"))
+        assert np.abs(out["S"]).max() < 1e-16
+    assert np.abs(out["u"][0] - (0.02 + 9 * F[0])).max() < 1e-15
+
+
+@pytest.mark.parametrize("q", [19, 9])
+def test_bounce_back_conserves_mass(q):
+    """Halfway bounce-back on every face returns each outgoing population to its node: mass is
+    conserved to rounding (momentum is not, by design)."""
+    dims = (5, 6, 4) if q == 19 else (8, 6, 1)
+    p = O.make_params(q, rates(q), bc=[O.WALL] * 6, formula=O.CHAI)
+    G = O.Grid(p, *dims)
+    f = I.random_populations(q, G.shape, scale=2e-3, seed=5)
+    m0 = G.sums(f)[0]
+    for _ in range(4):
+        f, _ = G.step(f)
+    assert abs(G.sums(f)[0] - m0) < 1e-13 * G.N * np.abs(f).max()
+
+
+def test_axis_permutation_symmetry():
+    """The physics is invariant under a cyclic relabelling of the axes x -> y -> z: the TGV
+    rotated that way gives the strain rate with its components rotated.  A swapped or
+    mis-signed component in either formula breaks this."""
+    n = 6
+    drho, u, g = I.taylor_green_3d(n, u0=0.03, pressure=True)
+    for formula in (O.YU, O.CHAI):
+        p = O.make_params(19, rates(19), formula=formula)
+        G = O.Grid(p, n, n, n)
+        f = G.init(drho, u, g)
+        f = G.run(f, 3)
+        S = G.readout(f)["S"]
+        # relabel old axis a as new axis perm[a] (x -> y, y -> z, z -> x).  Arrays are indexed
+        # [z, y, x], so the relabelled array is B[i, j, k] = A[k, i, j] = transpose(A, (1, 2, 0)).
+        up = np.zeros_like(u)
+        up[1] = np.transpose(u[0], (1, 2, 0))
+        up[2] = np.transpose(u[1], (1, 2, 0))
+        up[0] = np.transpose(u[2], (1, 2, 0))
+        gp = np.zeros_like(g)
+        perm = [1, 2, 0]  # old axis a -> new axis perm[a]
+        for a in range(3):
+            for b in range(3):
+                gp[perm[a] * 3 + perm[b]] = np.transpose(g[a * 3 + b], (1, 2, 0))
+        dp = np.transpose(drho, (1, 2, 0))
+        f2 = G.init(dp, up, gp)
+        f2 = G.run(f2, 3)
+        S2 = G.readout(f2)["S"]
+        # components: xx yy zz xy yz xz ; old (a,b) -> new (perm a, perm b)
+        names = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (0, 1): 3, (1, 2): 4, (0, 2): 5}
+        for (a, b), k in names.items():
+            na, nb = sorted((perm[a], perm[b]))
+            k2 = names[(na, nb)]
+            assert np.abs(S2[k2] - np.transpose(S[k], (1, 2, 0))).max() < 1e-15
+
+
+# ------------------------------------------------------------------------------------------------
+# closures
+
+
+def test_smagorinsky_zero_constant_is_newtonian():
+    n = 6
+    drho, u, g = I.taylor_green_3d(n, u0=0.03)
+    pn = O.make_params(19, rates(19, 0.51))
+    ps = O.make_params(19, rates(19, 0.51), closure=O.SMAG, smag_cs=0.0)
+    Gn, Gs = O.Grid(pn, n, n, n), O.Grid(ps, n, n, n)
+    f = Gn.init(drho, u, g)
+    a = Gn.run(f, 2)
+    b = Gs.run(f, 2)
+    assert np.array_equal(a, b)
+
+
+def test_smagorinsky_fixed_point_converged():
+    """The Smagorinsky closure tau = tau0 + 3 Cs^2 |S(1/tau)| is solved by 6 fixed-point sweeps;
+    at workload-like strain rates 6 and 30 sweeps agree to rounding and the residual vanishes."""
+    n = 12
+    drho, u, g = I.taylor_green_3d(n, u0=0.03, pressure=True)
+    out = []
+    for K in (6, 30):
+        for formula in (O.YU, O.CHAI):
+            p = O.make_params(19, rates(19, 0.51), closure=O.SMAG, smag_cs=0.17, smag_iters=K, formula=formula)
+            G = O.Grid(p, n, n, n)
+            f = G.init(drho, u, g)
+            f = G.run(f, 2)
+            r = G.readout(f)
+            Sn = np.sqrt(2 * ((r["S"][:3] ** 2).sum(0) + 2 * (r["S"][3:] ** 2).sum(0)))
+            resid = r["tau"] - (0.51 + 3 * 0.17 ** 2 * Sn)
+            assert np.abs(resid).max() < 1e-15
+            assert r["tau"].max() > 0.51 + 1e-4  # the closure is active
+            out.append(r)
+    assert np.abs(out[0]["S"] - out[2]["S"]).max() < 4e-15 * np.abs(out[0]["S"]).max()
+
+
+def test_power_law_index_one_is_newtonian():
+    """n = 1 gives nu = K, tau = 1/2 + 3K: the same step as the Newtonian model at that tau."""
+    K = 0.2048
+    tau = 0.5 + 3 * K
+    pn = O.make_params(9, rates(9, tau), formula=O.CHAI)
+    pp = O.make_params(9, rates(9, tau), formula=O.CHAI, closure=O.POWERLAW, pl_n=1.0, pl_k=K)
+    drho, u, g = I.taylor_green_2d(16, 16, u0=0.02)
+    Gn, Gp = O.Grid(pn, 16, 16, 1), O.Grid(pp, 16, 16, 1)
+    f = Gn.init(drho, u, g)
+    a = Gn.run(f, 3)
+    b = Gp.run(f, 3)
+    assert np.abs(a - b).max() < 1e-17
+
+
+@pytest.mark.parametrize("n_index", [0.5, 1.5])
+def test_power_law_fixed_point(n_index):
+    """The power-law closure returns tau with tau = clamp(1/2 + 3 K |S(1/tau)|^(n-1)) to the
+    iteration tolerance; at rest (S = 0) and n < 1 the clamp gives tau_max."""
+    U, L, Re = 0.05, 64, 100.0
+    K = U ** (2 - n_index) * L ** n_index / Re
+    p = O.make_params(9, rates(9, 0.5 + 3 * U * L / Re), formula=O.CHAI, closure=O.POWERLAW, pl_n=n_index,
+                      pl_k=K, pl_tau_min=0.505, pl_tau_max=5.0, pl_tol=1e-14)
+    drho, u, g = I.taylor_green_2d(16, 16, u0=0.02)
+    G = O.Grid(p, 16, 16, 1)
+    f = G.init(drho, u, g)
+    f = G.run(f, 2)
+    r = G.readout(f)
+    S = r["S"]
+    gd = np.sqrt(2 * (S[0] ** 2 + S[1] ** 2 + 2 * S[2] ** 2))
+    want = np.clip(0.5 + 3 * K * gd ** (n_index - 1), 0.505, 5.0)
+    assert np.abs(r["tau"] - want).max() < 1e-12 * r["tau"].max()
+    # fluid at rest
+    f0 = G.init(np.zeros((1, 16, 16)), np.zeros((2, 1, 16, 16)))
+    r0 = G.readout(f0)
+    assert np.all(r0["tau"] == (5.0 if n_index < 1 else 0.505))
+
+
+# ------------------------------------------------------------------------------------------------
+# exact flows
+
+
+@pytest.mark.parametrize("q", [19, 9])
+def test_initial_strain_equals_analytic(q):
+    """Initialisation by the first-order non-equilibrium moments (eq. (YuLuobasis)) gives a state
+    whose strain rate by either formula is the prescribed velocity gradient's symmetric part."""
+    if q == 19:
+        cases = [I.taylor_green_3d(8, u0=0.03), I.abc_flow(8, u0=0.03)]
+        dims = (8, 8, 8)
+    else:
+        cases = [I.taylor_green_2d(12, 12, u0=0.03)]
+        dims = (12, 12, 1)
+    for closure in (O.NEWTON, O.SMAG):
+        for drho, u, g in cases:
+            for formula in (O.YU, O.CHAI):
+                p = O.make_params(q, rates(q), formula=formula, closure=closure, smag_cs=0.17)
+                G = O.Grid(p, *dims)
+                f = G.init(drho, u, g)
+                r = G.readout(f)
+                Sa = strain_from_grad(q, g)
+                assert np.abs(r["S"] - Sa).max() < 1e-14 * np.abs(Sa).max()
+                assert np.abs(r["u"] - u).max() < 1e-16
+
+
+@pytest.mark.parametrize("plane,dims", [("xy", (16, 16, 2)), ("yz", (2, 16, 16)), ("xz", (16, 2, 16))])
+def test_taylor_green_decay_in_each_plane(plane, dims):
+    """The 2D Taylor-Green vortex is an exact Navier-Stokes solution whose strain rate decays as
+    exp(-2 nu k^2 t), nu = (tau - 1/2)/3.  Run in each coordinate plane of the D3Q19 lattice
+    (exercising every strain component) both routes reproduce the analytic field to the
+    scheme's second-order accuracy (measured 1.3e-2 relative at n = 16 after 50 steps)."""
+    n = 16
+    drho, u, g = I.taylor_green_2d(*dims, u0=0.01, plane=plane)
+    nu = (TAU - 0.5) / 3
+    k = 2 * np.pi / n
+    T = 50
+    dec = np.exp(-2 * nu * k * k * T)
+    Sa = strain_from_grad(19, g) * dec
+    for formula in (O.YU, O.CHAI):
+        p = O.make_params(19, rates(19), formula=formula)
+        G = O.Grid(p, *dims)
+        f = G.init(drho, u, g)
+        f = G.run(f, T)
+        S = G.readout(f)["S"]
+        err = np.abs(S - Sa).max() / np.abs(Sa).max()
+        assert err < 2e-2
+        # the shear components that involve the axis normal to the plane stay zero
+        normal = {"xy": 2, "yz": 0, "xz": 1}[plane]
+        pairs = {3: (0, 1), 4: (1, 2), 5: (0, 2)}
+        off = [k2 for k2, ab in pairs.items() if normal in ab]
+        assert np.abs(S[off]).max() < 1e-15
+
+
+def test_abc_flow_decay():
+    """Arnold-Beltrami-Childress flow: exact Navier-Stokes solution decaying as exp(-nu k^2 t)."""
+    n = 12
+    drho, u, g = I.abc_flow(n, u0=0.01)
+    nu = (TAU - 0.5) / 3
+    k = 2 * np.pi / n
+    T = 30
+    Sa = strain_from_grad(19, g) * np.exp(-nu * k * k * T)
+    p = O.make_params(19, rates(19), formula=O.YU)
+    G = O.Grid(p, n, n, n)
+    f = G.run(G.init(drho, u, g), T)
+    S = G.readout(f)["S"]
+    assert np.abs(S - Sa).max() / np.abs(Sa).max() < 3e-2
+
+
+@pytest.mark.parametrize("q", [19, 9])
+def test_second_order_convergence(q):
+    """Sec. 5.1: the strain rate is second-order accurate in space.  Diffusive scaling
+    (u0 ~ 1/n, steps ~ n^2) of the 2D Taylor-Green vortex: the relative L2 error of S falls by
+    a factor of at least 2^1.9 per grid doubling."""
+    errs = []
+    for n in (8, 16, 32):
+        u0 = 0.04 * 8 / n
+        T = int(10 * (n / 8) ** 2)
+        dims = (n, n, 1) if q == 9 else (n, n, 2)
+        p = O.make_params(q, rates(q), formula=O.CHAI)
+        G = O.Grid(p, *dims)
+        drho, u, g = I.taylor_green_2d(*dims, u0=u0, plane="xy")
+        f = G.run(G.init(drho, u, g), T)
+        nu = (TAU - 0.5) / 3
+        k = 2 * np.pi / n
+        Sa = strain_from_grad(q, g) * np.exp(-2 * nu * k * k * T)
+        S = G.readout(f)["S"]
+        errs.append(np.sqrt(((S - Sa) ** 2).sum() / (Sa ** 2).sum()))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert slopes.min() >= 1.9, (errs, slopes)
+
+
+@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("formula", [O.YU, O.CHAI])
+def test_poiseuille_channel(q, formula):
+    """Force-driven channel between halfway bounce-back walls: in the steady state the shear
+    rate is exactly linear, S_xy = -(g / 2 nu)(y - y_c), by the momentum balance; S_yy = 0; the
+    normal stress S_xx is a second-order effect of the scheme, bounded by |S_xy|^2."""
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    H, g = 16, 1e-6
+    d = 3 if q == 19 else 2
+    F = np.zeros(d)
+    F[0] = g
+    p = O.make_params(q, rates(q, tau), bc=CHANNEL, formula=formula)
+    G = O.Grid(p, 1, H, 1)
+    f = G.init(np.zeros((1, H, 1)), np.zeros((d, 1, H, 1)), force=F)
+    f = G.run(f, 6000, force=F)
+    S = G.readout(f, force=F)["S"][:, 0, :, 0]
+    y = np.arange(H)
+    Sxy = -(g / (2 * nu)) * (y - (H - 1) / 2)
+    ixy = 3 if q == 19 else 2
+    assert np.abs(S[ixy] - Sxy).max() < 1e-9 * np.abs(Sxy).max()
+    assert np.abs(S[1]).max() < 1e-14 * np.abs(Sxy).max()
+    assert np.abs(S[0]).max() < 2.0 * np.abs(Sxy).max() ** 2
+
+
+@pytest.mark.parametrize("q", [19, 9])
+def test_couette_moving_lid(q):
+    """Plane Couette flow between a wall at y = -1/2 and a lid moving at U at y = H - 1/2:
+    steady u_x = U (y + 1/2)/H and uniform S_xy = U / (2H) (halfway bounce-back with the moving
+    wall term is exact for a linear profile)."""
+    d = 3 if q == 19 else 2
+    H, U = 16, 0.01
+    lid = [[0.0, 0.0, 0.0] for _ in range(6)]
+    lid[3] = [U, 0.0, 0.0]
+    p = O.make_params(q, rates(q, 0.8), bc=[O.PERIODIC, O.PERIODIC, O.WALL, O.LID, O.PERIODIC, O.PERIODIC],
+                      lid_u=lid)
+    G = O.Grid(p, 1, H, 1)
+    f = G.run(G.init(np.zeros((1, H, 1)), np.zeros((d, 1, H, 1))), 6000)
+    r = G.readout(f)
+    ixy = 3 if q == 19 else 2
+    assert np.abs(r["S"][ixy] - U / (2 * H)).max() < 1e-9 * U / (2 * H)
+    y = np.arange(H)
+    assert np.abs(r["u"][0, 0, :, 0] - U * (y + 0.5) / H).max() < 1e-9 * U
