@@ -1,0 +1,175 @@
+/*
+ * lbm.h -- C ABI of the GB300 MRT lattice Boltzmann library (liblbm.so).
+ *
+ * The library runs the fused multiple-relaxation-time (MRT) lattice Boltzmann time step of the
+ * He-Luo D3Q19 model (and its D2Q9 counterpart) on one NVIDIA GPU, forming the strain-rate
+ * tensor S at every node by either of the two routes compared by Zhang, Huang, Wang and Shi,
+ * "The computation of strain rate tensor in multiple-relaxation-time lattice Boltzmann model"
+ * (arXiv:1704.07559):
+ *   LBM_YU    Yu's formula, eq. (LuoS): S from six non-equilibrium moments;
+ *   LBM_CHAI  Chai's formula, eq. (ChaiS): S from the nineteen non-equilibrium distributions,
+ *             -sum_i c_i c_i (T^-1 L T f_neq)_i / (2 rho0 cs^2).
+ * S feeds a strain-rate-dependent relaxation time (Smagorinsky eddy viscosity or a power-law
+ * fluid) inside the same step.
+ *
+ * Conventions shared by every call
+ *  - Lattice units: delta_x = delta_t = 1, cs^2 = 1/3, nu = (tau - 1/2)/3.
+ *  - Populations are the delta-rho form of Sec. 2, eq. (edf): sum_i f_i = delta rho.  They live
+ *    in two caller-owned device buffers ("A" and "B"), each holding q population arrays of
+ *    `stride` elements (lbm_layout), element (i, node) at i*stride + node, node =
+ *    (z*ny + y)*nx + x.  The element type is the storage precision: double (LBM_FP64), float
+ *    (LBM_FP32), IEEE half (LBM_FP16S) or bfloat16 (LBM_BF16S).  The arithmetic is double for
+ *    LBM_FP64 and float for the other three ("compute type" below).
+ *  - The buffer most recently written holds the post-collision populations f* of the last step.
+ *    Read-outs (lbm_strain_rate, lbm_macroscopic, lbm_sums) report the pre-collision state that
+ *    the next step sees, obtained by pulling f_i(x) = f*_i(x - c_i) with the boundary rules.
+ *  - Fields passed in or out are dense component-major arrays: component c of node n at c*N + n,
+ *    N = nx*ny*nz.  Strain components are xx, yy, zz, xy, yz, xz in 3D and xx, yy, xy in 2D.
+ *  - Faces are numbered -x, +x, -y, +y, -z, +z.  Opposite faces must both be periodic or both
+ *    not.  A wall is halfway bounce-back; a moving wall ("lid") adds 2 w_i rho0 (c_i . u_w)/cs^2
+ *    to the population it reflects; a population that leaves through an edge or corner where
+ *    two non-periodic faces meet is reflected without the moving-wall term.
+ *  - All calls are asynchronous on the bound stream unless stated otherwise, return LBM_OK or a
+ *    negative status, never abort, and leave a message for lbm_last_error.
+ *  - A context is not thread-safe: calls on one context must not run concurrently.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_ERR_ARG -1       /* invalid argument: nothing was done */
+#define LBM_ERR_CUDA -2      /* a CUDA runtime call or kernel launch failed */
+#define LBM_ERR_NOMEM -3     /* the library's own small allocation failed */
+#define LBM_ERR_NONFINITE -4 /* a global sum came back NaN or infinite */
+#define LBM_ERR_STATE -5     /* call out of order (e.g. lbm_step before lbm_bind) */
+
+/* lattices (the value is q) */
+#define LBM_D2Q9 9
+#define LBM_D3Q19 19
+
+/* population storage precision */
+#define LBM_FP64 0
+#define LBM_FP32 1
+#define LBM_FP16S 2 /* IEEE binary16 storage of the delta-rho form, float arithmetic */
+#define LBM_BF16S 3 /* bfloat16 storage of the delta-rho form, float arithmetic */
+
+/* closures for the viscous relaxation rate s_nu = 1/tau */
+#define LBM_NEWTON 0   /* tau fixed by the rates given to lbm_create */
+#define LBM_SMAG 1     /* tau = tau0 + 3 Cs^2 |S| (filter width 1) */
+#define LBM_POWERLAW 2 /* tau = 1/2 + 3 K |S|^(n-1), clamped to [tau_min, tau_max] */
+
+/* strain-rate routes */
+#define LBM_YU 0
+#define LBM_CHAI 1
+
+/* boundary kinds per face */
+#define LBM_PERIODIC 0
+#define LBM_WALL 1
+#define LBM_LID 2
+
+/* Model parameters (plain data, copied by lbm_create).  |S| = sqrt(2 S:S).  With a closure, S
+ * and tau are solved together at each node by fixed-point sweeps on tau from the same
+ * pre-collision state: Smagorinsky takes exactly smag_iters sweeps from tau0; the power law
+ * sweeps from tau0 until |tau_new - tau| <= pl_tol * tau_new or pl_max_iter sweeps. */
+typedef struct lbm_params {
+    int precision;   /* LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S */
+    int closure;     /* LBM_NEWTON, LBM_SMAG, LBM_POWERLAW */
+    int formula;     /* LBM_YU or LBM_CHAI: the route whose S feeds the closure in lbm_step */
+    int smag_iters;  /* Smagorinsky sweeps, 1..64 (default 6) */
+    int pl_max_iter; /* power-law sweep cap, 1..1000 (default 64) */
+    int bc[6];       /* per face: LBM_PERIODIC, LBM_WALL or LBM_LID (default all periodic) */
+    int force_field; /* 1: lbm_bind supplies a per-node force field; 0: the uniform force */
+    double rho0;     /* mean density (default 1) */
+    double smag_cs;  /* Smagorinsky constant Cs */
+    double pl_n;     /* power-law index n > 0 */
+    double pl_k;     /* power-law consistency K >= 0 */
+    double pl_tau_min, pl_tau_max; /* clamp, 1/2 < tau_min <= tau_max (default 0.505, 5.0) */
+    double pl_tol;   /* relative sweep tolerance (default 1e-13 for FP64, 1e-6 otherwise) */
+    double lid_u[6][3]; /* wall velocity of each LBM_LID face */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *p with the defaults named above (FP32, Newtonian, Yu, all faces periodic, rho0 = 1).
+ * p must not be NULL. */
+void lbm_default_params(lbm_params* p);
+
+/* Create a context for an nx x ny x nz lattice (nz = 1 for D2Q9).
+ *  lattice  LBM_D2Q9 or LBM_D3Q19.
+ *  rates    q relaxation rates s_0..s_{q-1} of the diagonal collision matrix, eq. (sD3Q15):
+ *           the conserved entries (0, 3, 5, 7 in D3Q19; 0, 3, 5 in D2Q9) must be 0, every other
+ *           entry lies in (0, 2).  The viscous entries (9, 11, 13, 14, 15 in D3Q19; 7, 8 in D2Q9)
+ *           hold 1/tau0; they must be equal for the Yu route and for any closure.
+ *  force    d components of a uniform body-force density (rho0 g), or NULL for none.
+ *  p        parameters, or NULL for the defaults.
+ * Host pointers, read during the call only.  Errors: LBM_ERR_ARG for any violated rule above,
+ * nx*ny*nz >= 2^31, or ny or nz > 65535; LBM_ERR_NOMEM / LBM_ERR_CUDA if the context's own
+ * device scratch (a few KB of partial sums) cannot be allocated.  *out is set to NULL on error. */
+int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double* rates,
+               const double* force, const lbm_params* p);
+
+/* Free the context and the scratch it allocated.  Caller-owned buffers are untouched.
+ * NULL is accepted. */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Population layout: q arrays of *stride elements of *elem_bytes bytes in each of the two
+ * buffers (stride >= N, a multiple of 128).  Any output pointer may be NULL. */
+int lbm_layout(const lbm_ctx* ctx, int* q, int64_t* stride, int* elem_bytes);
+
+/* Bind caller-owned device memory and a CUDA stream (cudaStream_t passed as void*, NULL = the
+ * legacy default stream).  f_a, f_b: q*stride elements each, 16-byte aligned, distinct.
+ * force_field: d x N values of the compute type when the context was created with
+ * p->force_field = 1 (must be non-NULL then), else ignored.  The buffers must stay valid until
+ * the context is destroyed or re-bound.  After binding, A is the current buffer. */
+int lbm_bind(lbm_ctx* ctx, void* f_a, void* f_b, const void* force_field, void* stream);
+
+/* Initialise the current buffer so that the next step sees the pre-collision state
+ *   f(x) = f_eq(drho, rho0 u) + T^-1 m_neq - Fbar/2,
+ * where m_neq holds the first-order viscous non-equilibrium moments of the velocity gradient
+ * given by eq. (YuLuobasis) of Sec. 4.1 (zero when grad_u is NULL) and Fbar is the discrete force.
+ * drho (N), u (d x N), grad_u (d*d x N, entry a*d + b = du_a/dx_b): device pointers to double.
+ * With a closure, s_nu in m_neq is the closure's value at the given gradient. */
+int lbm_init(lbm_ctx* ctx, const double* drho, const double* u, const double* grad_u);
+
+/* Advance n >= 0 time steps: each step pulls f from the current buffer, collides every node
+ * with S and tau formed by p->formula, and writes f* to the other buffer, which becomes current.
+ * n = 0 does nothing. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Strain rate of the state the next step sees, by `formula` (LBM_YU or LBM_CHAI), with the
+ * closure solved as in a step.  S_out: ns x N values of the compute type (ns = 6 in 3D, 3 in
+ * 2D); tau_out: N values or NULL.  Device pointers.  LBM_YU requires equal viscous rates. */
+int lbm_strain_rate(lbm_ctx* ctx, int formula, void* S_out, void* tau_out);
+
+/* Macroscopic fields of the state the next step sees: drho = sum f (N values) and
+ * u = (sum c f + F/2)/rho0 (d x N values), compute type, device pointers (either may be NULL). */
+int lbm_macroscopic(lbm_ctx* ctx, void* drho_out, void* u_out);
+
+/* Global sums of the state the next step sees, accumulated in FP64 on the device:
+ * out[0] = sum delta rho, out[1..d] = sum j (j = sum c f + F/2).  out is a HOST pointer to d+1
+ * doubles.  Synchronises the bound stream.  Returns LBM_ERR_NONFINITE (with out filled) if a sum
+ * is NaN or infinite. */
+int lbm_sums(lbm_ctx* ctx, double* out);
+
+/* Copy the current buffer's populations to dst / from src as a dense q x N array of the storage
+ * type (no stride padding).  dst/src may be host or device memory (pinned host memory gives
+ * asynchronous copies; pageable host memory makes the call synchronous). */
+int lbm_get_state(lbm_ctx* ctx, void* dst);
+int lbm_set_state(lbm_ctx* ctx, const void* src);
+
+/* Message of the last failed call on ctx (empty if none), owned by the context.  With ctx = NULL:
+ * the message of the last failed lbm_create on the calling thread. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

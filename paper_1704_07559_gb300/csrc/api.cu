@@ -1,0 +1,449 @@
+// api.cu -- the C ABI declared in include/lbm.h: argument checks, the context, and dispatch to
+// the kernel instantiations.  No call aborts; every failure returns a status and a message.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "launch.h"
+#include "step.cuh"
+
+struct lbm_ctx {
+    int q, d, ns;
+    int nx, ny, nz;
+    long long N, stride;
+    int elem_bytes;
+    double rates[19];
+    double force[3];
+    lbm_params p;
+    // bound resources
+    void* buf[2];
+    const void* force_field;
+    cudaStream_t stream;
+    int bound;
+    int cur;  // index of the current buffer
+    // library-owned scratch: per-block partial sums and the final row
+    double* partial;
+    double* result;
+    char err[512];
+};
+
+namespace {
+
+// message of the last failed lbm_create on this thread (lbm_last_error(NULL) returns it)
+thread_local char create_err[256] = "";
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+bool is_viscous(int q, int k) {
+    return q == 19 ? (k == 9 || k == 11 || k == 13 || k == 14 || k == 15) : (k == 7 || k == 8);
+}
+bool is_conserved(int q, int k) {
+    return q == 19 ? (k == 0 || k == 3 || k == 5 || k == 7) : (k == 0 || k == 3 || k == 5);
+}
+int first_viscous(int q) { return q == 19 ? 9 : 7; }
+
+bool viscous_rates_equal(const lbm_ctx* c) {
+    const double s = c->rates[first_viscous(c->q)];
+    for (int k = 0; k < c->q; ++k)
+        if (is_viscous(c->q, k) && c->rates[k] != s) return false;
+    return true;
+}
+
+template <class R>
+void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
+    std::memset(a, 0, sizeof(*a));
+    a->nx = c->nx;
+    a->ny = c->ny;
+    a->nz = c->nz;
+    a->stride = c->stride;
+    for (int k = 0; k < 19; ++k) a->s[k] = R(k < c->q ? c->rates[k] : 0.0);
+    for (int d = 0; d < 3; ++d) a->F[d] = R(c->force[d]);
+    a->rho0 = R(c->p.rho0);
+    a->inv_rho0 = R(1.0 / c->p.rho0);
+    a->tau0 = R(1.0 / c->rates[first_viscous(c->q)]);
+    a->smag_c3 = R(3.0 * c->p.smag_cs * c->p.smag_cs);
+    a->pl_k3 = R(3.0 * c->p.pl_k);
+    a->pl_nm1 = R(c->p.pl_n - 1.0);
+    a->pl_tau_min = R(c->p.pl_tau_min);
+    a->pl_tau_max = R(c->p.pl_tau_max);
+    a->pl_tol = R(c->p.pl_tol);
+    a->smag_iters = c->p.smag_iters;
+    a->pl_max_iter = c->p.pl_max_iter;
+    int wall = 0, lid = 0;
+    for (int f = 0; f < 6; ++f) {
+        if (c->d == 2 && f >= 4) continue;
+        if (c->p.bc[f] != LBM_PERIODIC) wall |= 1 << f;
+        if (c->p.bc[f] == LBM_LID) lid |= 1 << f;
+        for (int k = 0; k < 3; ++k) a->lid[f][k] = R(c->p.lid_u[f][k]);
+    }
+    a->wall_mask = wall;
+    a->lid_mask = lid;
+    a->force_field = c->p.force_field ? static_cast<const R*>(c->force_field) : nullptr;
+}
+
+bool has_force(const lbm_ctx* c) {
+    return c->p.force_field || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
+}
+
+enum Tag { T_D3Q19_F64, T_D3Q19_F32, T_D3Q19_F16, T_D3Q19_BF16, T_D2Q9_F64, T_D2Q9_F32, T_NONE };
+
+Tag tag_of(int q, int precision) {
+    if (q == 19) {
+        switch (precision) {
+            case LBM_FP64: return T_D3Q19_F64;
+            case LBM_FP32: return T_D3Q19_F32;
+            case LBM_FP16S: return T_D3Q19_F16;
+            case LBM_BF16S: return T_D3Q19_BF16;
+        }
+    } else if (q == 9) {
+        switch (precision) {
+            case LBM_FP64: return T_D2Q9_F64;
+            case LBM_FP32: return T_D2Q9_F32;
+        }
+    }
+    return T_NONE;
+}
+
+// step or read-out launch through the right instantiation
+cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, void* drho, void* u,
+                     const void* src, void* dst) {
+    const int force = has_force(c) ? 1 : 0;
+    const Tag t = tag_of(c->q, c->p.precision);
+    if (c->p.precision == LBM_FP64) {
+        lbm::StepArgs<double> a;
+        fill_args(c, &a);
+        a.readout = readout;
+        a.src = src;
+        a.dst = dst;
+        a.S_out = static_cast<double*>(S);
+        a.tau_out = static_cast<double*>(tau);
+        a.drho_out = static_cast<double*>(drho);
+        a.u_out = static_cast<double*>(u);
+        return t == T_D3Q19_F64 ? lbm::step_d3q19_f64(a, c->p.closure, formula, force, c->stream)
+                                : lbm::step_d2q9_f64(a, c->p.closure, formula, force, c->stream);
+    }
+    lbm::StepArgs<float> a;
+    fill_args(c, &a);
+    a.readout = readout;
+    a.src = src;
+    a.dst = dst;
+    a.S_out = static_cast<float*>(S);
+    a.tau_out = static_cast<float*>(tau);
+    a.drho_out = static_cast<float*>(drho);
+    a.u_out = static_cast<float*>(u);
+    switch (t) {
+        case T_D3Q19_F32: return lbm::step_d3q19_f32(a, c->p.closure, formula, force, c->stream);
+        case T_D3Q19_F16: return lbm::step_d3q19_f16(a, c->p.closure, formula, force, c->stream);
+        case T_D3Q19_BF16: return lbm::step_d3q19_bf16(a, c->p.closure, formula, force, c->stream);
+        case T_D2Q9_F32: return lbm::step_d2q9_f32(a, c->p.closure, formula, force, c->stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int check_bound(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->bound) return fail(c, LBM_ERR_STATE, "no buffers bound (call lbm_bind first)");
+    return LBM_OK;
+}
+
+}  // namespace
+
+namespace lbm {
+__global__ void k_sums_final(const double* __restrict__ partial, int nblocks, int width, double* __restrict__ out) {
+    // one warp: lane c sums column c in block order (deterministic)
+    const int c = threadIdx.x;
+    if (c >= width) return;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += partial[b * width + c];
+    out[c] = v;
+}
+}  // namespace lbm
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->precision = LBM_FP32;
+    p->closure = LBM_NEWTON;
+    p->formula = LBM_YU;
+    p->smag_iters = 6;
+    p->pl_max_iter = 64;
+    for (int f = 0; f < 6; ++f) p->bc[f] = LBM_PERIODIC;
+    p->force_field = 0;
+    p->rho0 = 1.0;
+    p->smag_cs = 0.0;
+    p->pl_n = 1.0;
+    p->pl_k = 0.0;
+    p->pl_tau_min = 0.505;
+    p->pl_tau_max = 5.0;
+    p->pl_tol = -1.0;  // resolved by lbm_create from the precision
+}
+
+int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double* rates, const double* force,
+               const lbm_params* pin) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx;
+    if (!c) return LBM_ERR_NOMEM;
+    std::memset(c, 0, sizeof(*c));
+    auto bad = [&](const char* what) {
+        snprintf(create_err, sizeof(create_err), "lbm_create: invalid %s", what);
+        delete c;
+        return LBM_ERR_ARG;
+    };
+    create_err[0] = '\0';
+    if (lattice != LBM_D3Q19 && lattice != LBM_D2Q9) return bad("lattice");
+    c->q = lattice;
+    c->d = lattice == LBM_D3Q19 ? 3 : 2;
+    c->ns = lattice == LBM_D3Q19 ? 6 : 3;
+    if (nx < 1 || ny < 1 || nz < 1) return bad("dims");
+    if (c->d == 2 && nz != 1) return bad("nz");
+    if (ny > 65535 || nz > 65535) return bad("ny/nz");
+    const long long N = (long long)nx * ny * nz;
+    if (N >= (1LL << 31)) return bad("N");
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = N;
+    c->stride = (N + 127) / 128 * 128;
+    if (!rates) return bad("rates");
+    if (pin)
+        c->p = *pin;
+    else
+        lbm_default_params(&c->p);
+    lbm_params& p = c->p;
+    for (int k = 0; k < c->q; ++k) {
+        const double s = rates[k];
+        if (!is_finite(s)) return bad("rate");
+        if (is_conserved(c->q, k)) {
+            if (s != 0.0) return bad("conserved rate");
+        } else if (!(s > 0.0 && s < 2.0)) {
+            return bad("rate range");
+        }
+        c->rates[k] = s;
+    }
+    for (int d = 0; d < 3; ++d) c->force[d] = (force && d < c->d) ? force[d] : 0.0;
+    for (int d = 0; d < 3; ++d)
+        if (!is_finite(c->force[d])) return bad("force");
+    switch (p.precision) {
+        case LBM_FP64: c->elem_bytes = 8; break;
+        case LBM_FP32: c->elem_bytes = 4; break;
+        case LBM_FP16S:
+        case LBM_BF16S: c->elem_bytes = 2; break;
+        default: return bad("precision");
+    }
+    if (tag_of(c->q, p.precision) == T_NONE) return bad("lattice/precision");
+    if (p.closure < LBM_NEWTON || p.closure > LBM_POWERLAW) return bad("closure");
+    if ((p.precision == LBM_FP16S || p.precision == LBM_BF16S) && p.closure == LBM_POWERLAW) return bad("16-bit power law");
+    if (p.formula != LBM_YU && p.formula != LBM_CHAI) return bad("formula");
+    if ((p.closure != LBM_NEWTON || p.formula == LBM_YU) && !viscous_rates_equal(c)) return bad("viscous rates");
+    if (!(p.rho0 > 0.0) || !is_finite(p.rho0)) return bad("rho0");
+    if (p.smag_iters < 1 || p.smag_iters > 64) return bad("smag_iters");
+    if (p.pl_max_iter < 1 || p.pl_max_iter > 1000) return bad("pl_max_iter");
+    if (!is_finite(p.smag_cs) || p.smag_cs < 0.0) return bad("smag_cs");
+    if (p.closure == LBM_POWERLAW) {
+        if (!(p.pl_n > 0.0) || !is_finite(p.pl_n) || !(p.pl_k >= 0.0) || !is_finite(p.pl_k)) return bad("power law");
+        if (!(p.pl_tau_min > 0.5) || !(p.pl_tau_max >= p.pl_tau_min) || !is_finite(p.pl_tau_max)) return bad("clamp");
+    }
+    if (p.pl_tol < 0.0) p.pl_tol = p.precision == LBM_FP64 ? 1e-13 : 1e-6;
+    if (!is_finite(p.pl_tol)) return bad("pl_tol");
+    for (int a = 0; a < c->d; ++a) {
+        const int f0 = p.bc[2 * a], f1 = p.bc[2 * a + 1];
+        if (f0 < LBM_PERIODIC || f0 > LBM_LID || f1 < LBM_PERIODIC || f1 > LBM_LID) return bad("bc");
+        if ((f0 == LBM_PERIODIC) != (f1 == LBM_PERIODIC)) return bad("bc pair");
+    }
+    if (c->d == 2) p.bc[4] = p.bc[5] = LBM_PERIODIC;
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k)
+            if (!is_finite(p.lid_u[f][k])) return bad("lid");
+    if (p.force_field != 0 && p.force_field != 1) return bad("force_field");
+
+    // library-owned scratch for the global sums
+    cudaError_t e = cudaMalloc(&c->partial, sizeof(double) * (size_t)lbm::SUM_BLOCKS * (1 + c->d));
+    if (e == cudaSuccess) e = cudaMalloc(&c->result, sizeof(double) * 4);
+    if (e != cudaSuccess) {
+        snprintf(create_err, sizeof(create_err), "lbm_create: scratch allocation failed: %s", cudaGetErrorString(e));
+        cudaFree(c->partial);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA;
+    }
+    c->err[0] = '\0';
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    cudaFree(c->partial);
+    cudaFree(c->result);
+    delete c;
+    return LBM_OK;
+}
+
+int lbm_layout(const lbm_ctx* c, int* q, int64_t* stride, int* elem_bytes) {
+    if (!c) return LBM_ERR_ARG;
+    if (q) *q = c->q;
+    if (stride) *stride = c->stride;
+    if (elem_bytes) *elem_bytes = c->elem_bytes;
+    return LBM_OK;
+}
+
+int lbm_bind(lbm_ctx* c, void* f_a, void* f_b, const void* force_field, void* stream) {
+    if (!c) return LBM_ERR_ARG;
+    if (!f_a || !f_b || f_a == f_b) return fail(c, LBM_ERR_ARG, "lbm_bind: need two distinct buffers");
+    if (((uintptr_t)f_a | (uintptr_t)f_b) & 15) return fail(c, LBM_ERR_ARG, "lbm_bind: buffers must be 16-byte aligned");
+    if (c->p.force_field && !force_field) return fail(c, LBM_ERR_ARG, "lbm_bind: force field required");
+    c->buf[0] = f_a;
+    c->buf[1] = f_b;
+    c->force_field = c->p.force_field ? force_field : nullptr;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->bound = 1;
+    c->cur = 0;
+    c->err[0] = '\0';
+    return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad_u) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!drho || !u) return fail(c, LBM_ERR_ARG, "lbm_init: drho and u are required");
+    lbm::StepArgs<double> a;
+    fill_args(c, &a);
+    a.dst = c->buf[c->cur];
+    cudaError_t e;
+    const Tag t = tag_of(c->q, c->p.precision);
+    switch (t) {
+        case T_D3Q19_F64:
+            e = lbm::init_d3q19_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
+            break;
+        case T_D2Q9_F64:
+            e = lbm::init_d2q9_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
+            break;
+        case T_D3Q19_F32:
+            e = lbm::init_d3q19_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            break;
+        case T_D3Q19_F16:
+            e = lbm::init_d3q19_f16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            break;
+        case T_D3Q19_BF16:
+            e = lbm::init_d3q19_bf16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            break;
+        case T_D2Q9_F32:
+            e = lbm::init_d2q9_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            break;
+        default: return fail(c, LBM_ERR_ARG, "lbm_init: unsupported lattice/precision");
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_init");
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (n < 0) return fail(c, LBM_ERR_ARG, "lbm_step: n < 0");
+    for (int it = 0; it < n; ++it) {
+        cudaError_t e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, c->buf[c->cur], c->buf[1 - c->cur]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
+        c->cur = 1 - c->cur;
+    }
+    return LBM_OK;
+}
+
+int lbm_strain_rate(lbm_ctx* c, int formula, void* S_out, void* tau_out) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (formula != LBM_YU && formula != LBM_CHAI) return fail(c, LBM_ERR_ARG, "lbm_strain_rate: formula");
+    if (!S_out) return fail(c, LBM_ERR_ARG, "lbm_strain_rate: S_out is required");
+    if (formula == LBM_YU && !viscous_rates_equal(c))
+        return fail(c, LBM_ERR_ARG, "lbm_strain_rate: Yu's formula needs equal viscous rates");
+    cudaError_t e = run_step(c, formula, 1, S_out, tau_out, nullptr, nullptr, c->buf[c->cur], nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_strain_rate");
+    return LBM_OK;
+}
+
+int lbm_macroscopic(lbm_ctx* c, void* drho_out, void* u_out) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!drho_out && !u_out) return LBM_OK;
+    cudaError_t e = run_step(c, c->p.formula, 1, nullptr, nullptr, drho_out, u_out, c->buf[c->cur], nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_macroscopic");
+    return LBM_OK;
+}
+
+int lbm_sums(lbm_ctx* c, double* out) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!out) return fail(c, LBM_ERR_ARG, "lbm_sums: out is required");
+    cudaError_t e;
+    const Tag t = tag_of(c->q, c->p.precision);
+    if (c->p.precision == LBM_FP64) {
+        lbm::StepArgs<double> a;
+        fill_args(c, &a);
+        a.src = c->buf[c->cur];
+        e = t == T_D3Q19_F64 ? lbm::sums_d3q19_f64(a, c->partial, c->result, c->stream)
+                             : lbm::sums_d2q9_f64(a, c->partial, c->result, c->stream);
+    } else {
+        lbm::StepArgs<float> a;
+        fill_args(c, &a);
+        a.src = c->buf[c->cur];
+        switch (t) {
+            case T_D3Q19_F32: e = lbm::sums_d3q19_f32(a, c->partial, c->result, c->stream); break;
+            case T_D3Q19_F16: e = lbm::sums_d3q19_f16(a, c->partial, c->result, c->stream); break;
+            case T_D3Q19_BF16: e = lbm::sums_d3q19_bf16(a, c->partial, c->result, c->stream); break;
+            case T_D2Q9_F32: e = lbm::sums_d2q9_f32(a, c->partial, c->result, c->stream); break;
+            default: e = cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums");
+    e = cudaMemcpyAsync(out, c->result, sizeof(double) * (1 + c->d), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums copy");
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums sync");
+    for (int k = 0; k <= c->d; ++k)
+        if (!is_finite(out[k])) return fail(c, LBM_ERR_NONFINITE, "lbm_sums: non-finite sum %d", k);
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx* c, void* dst) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!dst) return fail(c, LBM_ERR_ARG, "lbm_get_state: dst");
+    const size_t row = (size_t)c->N * c->elem_bytes, pitch = (size_t)c->stride * c->elem_bytes;
+    cudaError_t e = cudaMemcpy2DAsync(dst, row, c->buf[c->cur], pitch, row, c->q, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_state");
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx* c, const void* src) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!src) return fail(c, LBM_ERR_ARG, "lbm_set_state: src");
+    const size_t row = (size_t)c->N * c->elem_bytes, pitch = (size_t)c->stride * c->elem_bytes;
+    cudaError_t e = cudaMemcpy2DAsync(c->buf[c->cur], pitch, src, row, row, c->q, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_state");
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : create_err; }
+
+}  // extern "C"

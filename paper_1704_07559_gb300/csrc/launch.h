@@ -1,0 +1,37 @@
+// launch.h -- host-side entry points into the kernel instantiations, one set per
+// (lattice, storage precision).  Each returns the CUDA status of its launches.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+template <class R>
+struct StepArgs;
+
+// geometry of a lattice launch: 128-thread blocks covering x (and several y rows when nx is small)
+inline void lattice_grid(int nx, int ny, int nz, dim3* grid, dim3* block) {
+    const int bx = nx <= 32 ? 32 : (nx <= 64 ? 64 : 128);
+    const int by = 128 / bx;
+    *block = dim3(bx, by, 1);
+    *grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
+}
+
+constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in scratch
+
+#define LBM_DECLARE_ENTRY(TAG, R)                                                                         \
+    cudaError_t step_##TAG(const StepArgs<R>& a, int closure, int formula, int force, cudaStream_t s);   \
+    cudaError_t init_##TAG(const StepArgs<double>& a, int closure, const double* drho, const double* u, \
+                           const double* gu, const R* ffield, cudaStream_t s);                           \
+    cudaError_t sums_##TAG(const StepArgs<R>& a, double* partial, double* out, cudaStream_t s);
+
+LBM_DECLARE_ENTRY(d3q19_f64, double)
+LBM_DECLARE_ENTRY(d3q19_f32, float)
+LBM_DECLARE_ENTRY(d3q19_f16, float)
+LBM_DECLARE_ENTRY(d3q19_bf16, float)
+LBM_DECLARE_ENTRY(d2q9_f64, double)
+LBM_DECLARE_ENTRY(d2q9_f32, float)
+
+#undef LBM_DECLARE_ENTRY
+
+}  // namespace lbm

@@ -1,0 +1,800 @@
+// step.cuh -- the fused MRT lattice Boltzmann step and its read-out, init and sum kernels.
+//
+// One thread owns one lattice node.  A step pulls the node's 19 (or 9) pre-collision
+// populations from the previous post-collision buffer (f_i(x) = f*_i(x - c_i), Sec. 2
+// eq. (mrteq)), forms S by Yu's formula (eq. (LuoS)) or Chai's formula (eq. (ChaiS)), solves the
+// strain-rate closure for tau, relaxes in moment space (eq. (mrteqvT)) with the discrete force,
+// and stores f* at the node: a single pass over HBM, 2 q values per node.
+//
+// Both routes write the collision in "delta form", f* = f - (increment), so that the
+// storage-precision rounding acts only on the small collision increment:
+//   Yu route:   D_k = (s_k mneq_k - TF_k) / |T_k|^2 over moments k, mneq = T f - m_eq + TF/2,
+//               f*_i = f_i - sum_k T_ki D_k.
+//   Chai route: fneq_i = f_i - f_eq_i + Fbar_i/2;  Omega = T^-1 L T fneq;
+//               S = -sum_i c_i c_i Omega_i / (2 rho0 cs^2);  f*_i = f_i - Omega_i + Fbar_i.
+// TF = T Fbar is the moment vector of the Guo-type discrete force Fbar_i =
+// w_i[(c_i - u).F/cs^2 + (c_i.u)(c_i.F)/cs^4]; it equals the j-derivative of m_eq along F.
+// With a closure the viscous rates are unknown, so both routes split S = A + s_nu B (exact:
+// S is linear in the rates) and solve the scalar fixed point for tau = 1/s_nu.
+//
+// All lattice coefficients enter as compile-time constants: loops over populations and moments
+// are compile-time sequences (sfor) so each entry of T and c folds into an add, a subtract or
+// an FMA with an immediate.  Accumulators start at -0.0, the exact additive identity, so the
+// first term needs no special case.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+enum { CL_NEWTON = 0, CL_SMAG = 1, CL_POWERLAW = 2 };
+enum { F_YU = 0, F_CHAI = 1 };
+
+// ------------------------------------------------------------------------------------------
+// compile-time loops
+
+template <class F, int... Is>
+__host__ __device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+#define CV(x) (decltype(x)::value)
+
+// acc + t x for a compile-time integer t
+template <int T, class R>
+__device__ __forceinline__ R cadd(R acc, R x) {
+    if constexpr (T == 0)
+        return acc;
+    else if constexpr (T == 1)
+        return acc + x;
+    else if constexpr (T == -1)
+        return acc - x;
+    else
+        return acc + R(T) * x;
+}
+template <class R>
+__device__ __forceinline__ constexpr R nzero() {
+    return R(-0.0);
+}
+
+// ------------------------------------------------------------------------------------------
+// storage types
+
+template <class ST>
+struct Store;
+template <>
+struct Store<double> {
+    using R = double;
+    static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, R v) { __stcs(p, v); }
+};
+template <>
+struct Store<float> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, R v) { __stcs(p, v); }
+};
+template <>
+struct Store<__half> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
+};
+
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double r_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float r_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double r_abs(double x) { return fabs(x); }
+
+// ------------------------------------------------------------------------------------------
+// kernel arguments (by value)
+
+template <class R>
+struct StepArgs {
+    int nx, ny, nz;
+    int readout;          // 0: step (write f*); 1: write S/tau/drho/u of the pre-collision state
+    long long stride;     // elements between population arrays
+    const void* src;      // post-collision buffer of the previous step
+    void* dst;            // post-collision buffer of this step
+    const R* force_field; // d x N, or nullptr for the uniform force F
+    R F[3];
+    R s[19];              // relaxation rates; the viscous entries hold 1/tau0
+    R rho0, inv_rho0, tau0;
+    R smag_c3;            // 3 Cs^2
+    R pl_k3, pl_nm1, pl_tau_min, pl_tau_max, pl_tol;  // 3K, n-1, clamp, tolerance
+    int smag_iters, pl_max_iter;
+    int wall_mask;        // bit f: face f is not periodic (wall or lid)
+    int lid_mask;         // bit f: face f is a moving wall
+    R lid[6][3];
+    R* S_out;
+    R* tau_out;
+    R* drho_out;
+    R* u_out;
+};
+
+// ------------------------------------------------------------------------------------------
+// lattice-derived compile-time facts
+
+template <class L>
+__host__ __device__ constexpr int opp(int i) {
+    for (int p = 0; p < L::NP; ++p) {
+        if (L::pa(p) == i) return L::pb(p);
+        if (L::pb(p) == i) return L::pa(p);
+    }
+    return i;
+}
+
+// strain components: xx, yy, zz, xy, yz, xz (3D) or xx, yy, xy (2D)
+template <class L>
+__host__ __device__ constexpr int strain_axis(int cpt, int which) {
+    constexpr int ab3[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {1, 2}, {0, 2}};
+    constexpr int ab2[3][2] = {{0, 0}, {1, 1}, {0, 1}};
+    return L::NS == 6 ? ab3[cpt][which] : ab2[cpt][which];
+}
+
+// ------------------------------------------------------------------------------------------
+// moment transforms
+
+// m_K = sum_i T_Ki f_i from the rest population and the opposite-pair sums P / differences Dd
+template <class L, int K, class R>
+__device__ __forceinline__ R moment(R f0, const R (&P)[L::NP], const R (&Dd)[L::NP]) {
+    R acc = nzero<R>();
+    if constexpr (even_moment<L>(K)) {
+        acc = cadd<L::T(K, 0)>(acc, f0);
+        sfor<L::NP>([&](auto p) { acc = cadd<L::T(K, L::pa(CV(p)))>(acc, P[p]); });
+    } else {
+        sfor<L::NP>([&](auto p) { acc = cadd<L::T(K, L::pa(CV(p)))>(acc, Dd[p]); });
+    }
+    return acc;
+}
+
+// out_i = sum_k T_ki D_k over the moments k whose bit is set in USE, via even and odd parts of
+// each opposite pair
+template <class L, uint32_t USE, class R>
+__device__ __forceinline__ void back_transform(const R (&D)[L::Q], R (&out)[L::Q]) {
+    R r = nzero<R>();
+    sfor<L::Q>([&](auto k) {
+        if constexpr ((USE >> CV(k)) & 1u) r = cadd<L::T(CV(k), 0)>(r, D[k]);
+    });
+    out[0] = r;
+    sfor<L::NP>([&](auto p) {
+        constexpr int a = L::pa(CV(p)), b = L::pb(CV(p));
+        R E = nzero<R>(), O = nzero<R>();
+        sfor<L::Q>([&](auto k) {
+            if constexpr ((USE >> CV(k)) & 1u) {
+                if constexpr (even_moment<L>(CV(k)))
+                    E = cadd<L::T(CV(k), a)>(E, D[k]);
+                else
+                    O = cadd<L::T(CV(k), a)>(O, D[k]);
+            }
+        });
+        out[a] = E + O;
+        out[b] = E - O;
+    });
+}
+
+template <class L>
+__host__ __device__ constexpr uint32_t mask_nonconserved() {
+    uint32_t m = 0;
+    for (int k = 0; k < L::Q; ++k)
+        if (!L::conserved(k)) m |= 1u << k;
+    return m;
+}
+template <class L>
+__host__ __device__ constexpr uint32_t mask_viscous() {
+    uint32_t m = 0;
+    for (int k = 0; k < L::Q; ++k)
+        if (L::viscous(k)) m |= 1u << k;
+    return m;
+}
+
+// N_c = sum_i c_ia c_ib v_i for each strain component c = (a, b)
+template <class L, class R>
+__device__ __forceinline__ void contract(const R (&v)[L::Q], R (&N)[L::NS]) {
+    sfor<L::NS>([&](auto cpt) {
+        constexpr int a = strain_axis<L>(CV(cpt), 0), b = strain_axis<L>(CV(cpt), 1);
+        R acc = nzero<R>();
+        sfor<L::Q>([&](auto i) { acc = cadd<L::c(CV(i), a) * L::c(CV(i), b)>(acc, v[i]); });
+        N[cpt] = acc;
+    });
+}
+
+// ------------------------------------------------------------------------------------------
+// equilibrium moments (closed form) and force moments TF = d m_eq / d j . F
+
+template <class L>
+struct Eq;
+
+template <>
+struct Eq<D3Q19> {
+    // eq. (meq): w_eps = 3, w_epsj = -11/2, w_xx = -1/2
+    template <class R>
+    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], R ir0, R (&m)[19]) {
+        const R jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
+        m[0] = drho;
+        m[1] = R(-11) * drho + R(19) * jj;
+        m[2] = R(3) * drho - R(5.5) * jj;
+        m[3] = j[0];
+        m[4] = R(-2.0 / 3.0) * j[0];
+        m[5] = j[1];
+        m[6] = R(-2.0 / 3.0) * j[1];
+        m[7] = j[2];
+        m[8] = R(-2.0 / 3.0) * j[2];
+        m[9] = R(3) * j[0] * j[0] * ir0 - jj;
+        m[10] = R(-0.5) * m[9];
+        m[11] = (j[1] * j[1] - j[2] * j[2]) * ir0;
+        m[12] = R(-0.5) * m[11];
+        m[13] = j[0] * j[1] * ir0;
+        m[14] = j[1] * j[2] * ir0;
+        m[15] = j[0] * j[2] * ir0;
+        m[16] = R(0);
+        m[17] = R(0);
+        m[18] = R(0);
+    }
+    template <class R>
+    static __device__ __forceinline__ void tforce(const R (&j)[3], const R (&F)[3], R ir0, R (&t)[19]) {
+        const R jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
+        t[0] = R(0);
+        t[1] = R(38) * jF;
+        t[2] = R(-11) * jF;
+        t[3] = F[0];
+        t[4] = R(-2.0 / 3.0) * F[0];
+        t[5] = F[1];
+        t[6] = R(-2.0 / 3.0) * F[1];
+        t[7] = F[2];
+        t[8] = R(-2.0 / 3.0) * F[2];
+        t[9] = R(6) * j[0] * F[0] * ir0 - R(2) * jF;
+        t[10] = R(-0.5) * t[9];
+        t[11] = R(2) * (j[1] * F[1] - j[2] * F[2]) * ir0;
+        t[12] = R(-0.5) * t[11];
+        t[13] = (j[0] * F[1] + j[1] * F[0]) * ir0;
+        t[14] = (j[1] * F[2] + j[2] * F[1]) * ir0;
+        t[15] = (j[0] * F[2] + j[2] * F[0]) * ir0;
+        t[16] = R(0);
+        t[17] = R(0);
+        t[18] = R(0);
+    }
+    // Yu formula eq. (LuoS) split as S = A + s_nu B (A: the s1 m1 part)
+    template <class R>
+    static __device__ __forceinline__ void yu_split(const R (&mn)[19], R s1, R ir0, R (&A)[6], R (&B)[6]) {
+        const R a = -s1 * mn[1] * (R(1.0 / 38.0) * ir0);
+        A[0] = a;
+        A[1] = a;
+        A[2] = a;
+        A[3] = R(0);
+        A[4] = R(0);
+        A[5] = R(0);
+        B[0] = R(-0.5) * ir0 * mn[9];
+        B[1] = R(0.25) * ir0 * (mn[9] - R(3) * mn[11]);
+        B[2] = R(0.25) * ir0 * (mn[9] + R(3) * mn[11]);
+        B[3] = R(-1.5) * ir0 * mn[13];
+        B[4] = R(-1.5) * ir0 * mn[14];
+        B[5] = R(-1.5) * ir0 * mn[15];
+    }
+};
+
+template <>
+struct Eq<D2Q9> {
+    template <class R>
+    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], R ir0, R (&m)[9]) {
+        const R jj = (j[0] * j[0] + j[1] * j[1]) * ir0;
+        m[0] = drho;
+        m[1] = R(-2) * drho + R(3) * jj;
+        m[2] = drho - R(3) * jj;
+        m[3] = j[0];
+        m[4] = -j[0];
+        m[5] = j[1];
+        m[6] = -j[1];
+        m[7] = (j[0] * j[0] - j[1] * j[1]) * ir0;
+        m[8] = j[0] * j[1] * ir0;
+    }
+    template <class R>
+    static __device__ __forceinline__ void tforce(const R (&j)[3], const R (&F)[3], R ir0, R (&t)[9]) {
+        const R jF = (j[0] * F[0] + j[1] * F[1]) * ir0;
+        t[0] = R(0);
+        t[1] = R(6) * jF;
+        t[2] = R(-6) * jF;
+        t[3] = F[0];
+        t[4] = -F[0];
+        t[5] = F[1];
+        t[6] = -F[1];
+        t[7] = R(2) * (j[0] * F[0] - j[1] * F[1]) * ir0;
+        t[8] = (j[0] * F[1] + j[1] * F[0]) * ir0;
+    }
+    // Yu-type D2Q9 formula (Sec. 5.4 procedure): S_xx,yy = -(s_e m_e +- 3 s_nu m_pxx)/(4 rho0),
+    // S_xy = -3 s_nu m_pxy / (2 rho0)
+    template <class R>
+    static __device__ __forceinline__ void yu_split(const R (&mn)[9], R se, R ir0, R (&A)[3], R (&B)[3]) {
+        const R a = -se * mn[1] * (R(0.25) * ir0);
+        A[0] = a;
+        A[1] = a;
+        A[2] = R(0);
+        B[0] = R(-0.75) * ir0 * mn[7];
+        B[1] = R(0.75) * ir0 * mn[7];
+        B[2] = R(-1.5) * ir0 * mn[8];
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// closure: solve tau with S = A + (1/tau) B
+
+template <class L, class R>
+__device__ __forceinline__ R strain_norm(const R (&S)[L::NS]) {
+    R ss;
+    if constexpr (L::NS == 6)
+        ss = S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + R(2) * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]);
+    else
+        ss = S[0] * S[0] + S[1] * S[1] + R(2) * S[2] * S[2];
+    return r_sqrt(R(2) * ss);
+}
+
+template <class L, class R>
+__device__ __forceinline__ void affine(const R (&A)[L::NS], const R (&B)[L::NS], R s, R (&S)[L::NS]) {
+#pragma unroll
+    for (int c = 0; c < L::NS; ++c) S[c] = fma(s, B[c], A[c]);
+}
+
+// returns tau; S holds the strain rate at the returned tau
+template <class L, class R, int CLOSURE>
+__device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS], const StepArgs<R>& a,
+                                       R (&S)[L::NS]) {
+    if constexpr (CLOSURE == CL_NEWTON) {
+        affine<L>(A, B, a.s[L::NU0], S);
+        return a.tau0;
+    } else if constexpr (CLOSURE == CL_SMAG) {
+        R tau = a.tau0;
+        for (int it = 0; it < a.smag_iters; ++it) {
+            affine<L>(A, B, R(1) / tau, S);
+            tau = fma(a.smag_c3, strain_norm<L>(S), a.tau0);
+        }
+        affine<L>(A, B, R(1) / tau, S);
+        return tau;
+    } else {
+        R tau = a.tau0;
+        for (int it = 1; it <= a.pl_max_iter; ++it) {
+            affine<L>(A, B, R(1) / tau, S);
+            const R g = strain_norm<L>(S);
+            R tn = fma(a.pl_k3, r_pow(g, a.pl_nm1), R(0.5));
+            if (!(tn >= a.pl_tau_min)) tn = a.pl_tau_min;
+            if (tn > a.pl_tau_max) tn = a.pl_tau_max;
+            const R diff = r_abs(tn - tau);
+            tau = tn;
+            if (diff <= a.pl_tol * tn) break;
+        }
+        affine<L>(A, B, R(1) / tau, S);
+        return tau;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// pull streaming
+
+// Pre-collision populations of node (x,y,z).  Interior rows (y, z away from the faces, and x
+// away from non-periodic x faces) use wrapped x neighbours and direct row offsets; other nodes
+// take the general rule: periodic faces wrap, a population whose source lies behind a wall is
+// reflected from the opposite population of the same node, plus the moving-wall term when it
+// crosses exactly one moving face.
+template <class L, class ST, class R>
+__device__ __forceinline__ void pull(const StepArgs<R>& a, int x, int y, int z, R (&f)[L::Q]) {
+    const ST* __restrict__ src = static_cast<const ST*>(a.src);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long st = a.stride;
+    const int node = (z * ny + y) * nx + x;
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    const bool xwall = (a.wall_mask & 3) != 0;
+    bool fast = y > 0 && y < ny - 1 && (!xwall || (x > 0 && x < nx - 1));
+    if constexpr (L::D == 3) fast = fast && z > 0 && z < nz - 1;
+    if (fast) {
+        sfor<L::Q>([&](auto i) {
+            constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+            const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
+            const int row = ((z - cz) * ny + (y - cy)) * nx;
+            f[i] = Store<ST>::ld(src + CV(i) * st + row + sx);
+        });
+        return;
+    }
+    const int dims[3] = {nx, ny, nz};
+    const int pos[3] = {x, y, z};
+    sfor<L::Q>([&](auto i) {
+        int s[3];
+        int nout = 0, face = -1;
+        sfor<3>([&](auto ax) {
+            constexpr int cax = L::c(CV(i), CV(ax));
+            s[ax] = pos[ax] - cax;
+            if constexpr (cax != 0) {
+                if (s[ax] < 0 || s[ax] >= dims[ax]) {
+                    const int fc = 2 * CV(ax) + (s[ax] < 0 ? 0 : 1);
+                    if ((a.wall_mask >> fc) & 1) {
+                        ++nout;
+                        face = fc;
+                    } else {
+                        s[ax] = s[ax] < 0 ? s[ax] + dims[ax] : s[ax] - dims[ax];
+                    }
+                }
+            }
+        });
+        if (nout == 0) {
+            f[i] = Store<ST>::ld(src + CV(i) * st + (s[2] * ny + s[1]) * nx + s[0]);
+        } else {
+            R v = Store<ST>::ld(src + opp<L>(CV(i)) * st + node);
+            if (nout == 1 && ((a.lid_mask >> face) & 1)) {
+                const R cu = R(L::c(CV(i), 0)) * a.lid[face][0] + R(L::c(CV(i), 1)) * a.lid[face][1] +
+                             R(L::c(CV(i), 2)) * a.lid[face][2];
+                v += R(L::w36(CV(i)) / 6.0) * a.rho0 * cu;  // 2 w_i rho0 (c.u)/cs^2 = 6 w_i rho0 c.u
+            }
+            f[i] = v;
+        }
+    });
+}
+
+// ------------------------------------------------------------------------------------------
+// the fused step
+
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
+    using R = typename Store<ST>::R;
+    constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int N = a.nx * a.ny * a.nz;
+    const int node = (z * a.ny + y) * a.nx + x;
+
+    R f[Q];
+    pull<L, ST, R>(a, x, y, z, f);
+
+    // macroscopic: drho = sum f, j = sum c f + F/2 (from opposite-pair sums and differences)
+    R P[NP], Dd[NP];
+    sfor<NP>([&](auto p) {
+        P[p] = f[L::pa(CV(p))] + f[L::pb(CV(p))];
+        Dd[p] = f[L::pa(CV(p))] - f[L::pb(CV(p))];
+    });
+    R drho = f[0];
+    sfor<NP>([&](auto p) { drho += P[p]; });
+    R F[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) {
+        if (a.force_field) {
+            sfor<L::D>([&](auto d) { F[d] = a.force_field[CV(d) * N + node]; });
+        } else {
+            sfor<L::D>([&](auto d) { F[d] = a.F[d]; });
+        }
+    }
+    R j[3] = {R(0), R(0), R(0)};
+    sfor<L::D>([&](auto d) {
+        R acc = nzero<R>();
+        sfor<NP>([&](auto p) { acc = cadd<L::c(L::pa(CV(p)), CV(d))>(acc, Dd[p]); });
+        j[d] = FORCE ? fma(R(0.5), F[d], acc) : acc;
+    });
+    const R ir0 = a.inv_rho0;
+
+    R S[NS];
+    R tau;
+    R out[Q];  // f*_i = f_i - out_i
+
+    if constexpr (FORMULA == F_YU) {
+        R meq[Q], TF[Q], mn[Q];
+        Eq<L>::meq(drho, j, ir0, meq);
+        if constexpr (FORCE) Eq<L>::tforce(j, F, ir0, TF);
+        sfor<Q>([&](auto k) {
+            if constexpr (L::conserved(CV(k))) {
+                mn[k] = R(0);
+            } else {
+                const R m = moment<L, CV(k)>(f[0], P, Dd);
+                if constexpr (FORCE)
+                    mn[k] = fma(R(0.5), TF[k], m - meq[k]);
+                else
+                    mn[k] = m - meq[k];
+            }
+        });
+        R A[NS], B[NS];
+        Eq<L>::yu_split(mn, a.s[1], ir0, A, B);
+        tau = solve_tau<L, R, CLOSURE>(A, B, a, S);
+        if (a.readout) goto readout;
+        {
+            const R snu = CLOSURE == CL_NEWTON ? a.s[L::NU0] : R(1) / tau;
+            R Dk[Q];
+            sfor<Q>([&](auto k) {
+                constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
+                if constexpr (L::conserved(CV(k))) {
+                    if constexpr (FORCE)
+                        Dk[k] = -TF[k] * inv_n;
+                    else
+                        Dk[k] = R(0);
+                } else {
+                    const R sk = L::viscous(CV(k)) ? snu : a.s[k];
+                    if constexpr (FORCE)
+                        Dk[k] = fma(sk, mn[k], -TF[k]) * inv_n;
+                    else
+                        Dk[k] = sk * mn[k] * inv_n;
+                }
+            });
+            // with a force, the conserved moments 3, 5, 7 (D2Q9: 3, 5) carry -TF_k; TF_0 = 0
+            constexpr uint32_t use = FORCE ? (((1u << Q) - 1u) & ~1u) : mask_nonconserved<L>();
+            back_transform<L, use>(Dk, out);
+        }
+    } else {
+        // Chai route: non-equilibrium distributions, collision operator applied to them
+        R fneq[Q], g[Q];  // g_i = Fbar_i (kept for the collision)
+        {
+            const R jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
+            const R jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
+            sfor<Q>([&](auto i) {
+                constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+                constexpr R w = R(L::w36(CV(i)) / 36.0);
+                const R cj = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), j[0]), j[1]), j[2]);
+                const R feq = w * (drho + R(3) * cj + (R(4.5) * cj * cj) * ir0 - R(1.5) * jj);
+                if constexpr (FORCE) {
+                    const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
+                    const R fb = w * (R(3) * cF - R(3) * jF + (R(9) * cj * cF) * ir0);
+                    fneq[i] = fma(R(0.5), fb, f[i] - feq);
+                    g[i] = fb;
+                } else {
+                    fneq[i] = f[i] - feq;
+                    g[i] = R(0);
+                }
+            });
+        }
+        R Pn[NP], Dn[NP];
+        sfor<NP>([&](auto p) {
+            Pn[p] = fneq[L::pa(CV(p))] + fneq[L::pb(CV(p))];
+            Dn[p] = fneq[L::pa(CV(p))] - fneq[L::pb(CV(p))];
+        });
+        R mn[Q];
+        sfor<Q>([&](auto k) {
+            if constexpr (L::conserved(CV(k)))
+                mn[k] = R(0);
+            else
+                mn[k] = moment<L, CV(k)>(fneq[0], Pn, Dn);
+        });
+        const R kS = R(-1.5) * ir0;  // S = -N / (2 rho0 cs2)
+        if constexpr (CLOSURE == CL_NEWTON) {
+            R Dk[Q];
+            sfor<Q>([&](auto k) {
+                constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
+                if constexpr (L::conserved(CV(k)))
+                    Dk[k] = R(0);
+                else
+                    Dk[k] = a.s[k] * mn[k] * inv_n;
+            });
+            R Om[Q];
+            back_transform<L, mask_nonconserved<L>()>(Dk, Om);
+            R N[NS];
+            contract<L>(Om, N);
+#pragma unroll
+            for (int c = 0; c < NS; ++c) S[c] = kS * N[c];
+            tau = a.tau0;
+            if (a.readout) goto readout;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[i] = Om[i] - g[i];
+        } else {
+            R Df[Q], Dv[Q];
+            sfor<Q>([&](auto k) {
+                constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
+                if constexpr (L::conserved(CV(k)) || L::viscous(CV(k)))
+                    Df[k] = R(0);
+                else
+                    Df[k] = a.s[k] * mn[k] * inv_n;
+                if constexpr (L::viscous(CV(k)))
+                    Dv[k] = mn[k] * inv_n;
+                else
+                    Dv[k] = R(0);
+            });
+            R Of[Q], Ov[Q];
+            back_transform<L, mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Of);
+            back_transform<L, mask_viscous<L>()>(Dv, Ov);
+            R Nf[NS], Nv[NS], A[NS], B[NS];
+            contract<L>(Of, Nf);
+            contract<L>(Ov, Nv);
+#pragma unroll
+            for (int c = 0; c < NS; ++c) {
+                A[c] = kS * Nf[c];
+                B[c] = kS * Nv[c];
+            }
+            tau = solve_tau<L, R, CLOSURE>(A, B, a, S);
+            if (a.readout) goto readout;
+            const R snu = R(1) / tau;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[i] = fma(snu, Ov[i], Of[i]) - g[i];
+        }
+    }
+
+    {
+        ST* __restrict__ dst = static_cast<ST*>(a.dst);
+        sfor<Q>([&](auto i) { Store<ST>::st(dst + CV(i) * a.stride + node, f[i] - out[i]); });
+    }
+    return;
+
+readout:
+    if (a.S_out) {
+#pragma unroll
+        for (int c = 0; c < NS; ++c) a.S_out[c * N + node] = S[c];
+    }
+    if (a.tau_out) a.tau_out[node] = tau;
+    if (a.drho_out) a.drho_out[node] = drho;
+    if (a.u_out) {
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) a.u_out[d * N + node] = j[d] * ir0;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// initialisation from (drho, u, grad u), computed in double, un-streamed into the buffer
+
+template <class L, class ST>
+__global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int closure, const double* __restrict__ drho,
+                                              const double* __restrict__ u, const double* __restrict__ gu,
+                                              const typename Store<ST>::R* __restrict__ ffield) {
+    using R = typename Store<ST>::R;
+    constexpr int Q = L::Q, D = L::D;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, N = nx * ny * nz;
+    const int node = (z * ny + y) * nx + x;
+    const double r0 = a.rho0, ir0 = a.inv_rho0;
+    double j[3] = {0, 0, 0}, F[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) j[d] = r0 * u[d * N + node];
+    for (int d = 0; d < D; ++d) F[d] = ffield ? double(ffield[d * N + node]) : a.F[d];
+    const double dr = drho[node];
+    // first-order viscous non-equilibrium moments of the given gradient (eq. (YuLuobasis))
+    double mn[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) mn[k] = 0.0;
+    if (gu) {
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int p = 0; p < D; ++p)
+            for (int q = 0; q < D; ++q) G[p][q] = r0 * gu[(p * D + q) * N + node];
+        double snu = a.s[L::NU0];
+        if (closure != CL_NEWTON) {
+            double ss;
+            if (D == 3)
+                ss = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
+                     0.5 * ((G[0][1] + G[1][0]) * (G[0][1] + G[1][0]) + (G[1][2] + G[2][1]) * (G[1][2] + G[2][1]) +
+                            (G[0][2] + G[2][0]) * (G[0][2] + G[2][0]));
+            else
+                ss = G[0][0] * G[0][0] + G[1][1] * G[1][1] + 0.5 * (G[0][1] + G[1][0]) * (G[0][1] + G[1][0]);
+            const double gnorm = sqrt(2.0 * ss) * ir0;
+            double tau;
+            if (closure == CL_SMAG) {
+                tau = a.tau0 + a.smag_c3 * gnorm;
+            } else {
+                tau = 0.5 + a.pl_k3 * pow(gnorm, a.pl_nm1);
+                if (!(tau >= a.pl_tau_min)) tau = a.pl_tau_min;
+                if (tau > a.pl_tau_max) tau = a.pl_tau_max;
+            }
+            snu = 1.0 / tau;
+        }
+        const double divj = G[0][0] + G[1][1] + G[2][2];
+        if constexpr (Q == 19) {
+            mn[1] = -38.0 / (3.0 * a.s[1]) * divj;
+            mn[9] = -2.0 / (3.0 * snu) * (3.0 * G[0][0] - divj);
+            mn[11] = -2.0 / (3.0 * snu) * (G[1][1] - G[2][2]);
+            mn[13] = -(G[1][0] + G[0][1]) / (3.0 * snu);
+            mn[14] = -(G[2][1] + G[1][2]) / (3.0 * snu);
+            mn[15] = -(G[0][2] + G[2][0]) / (3.0 * snu);
+        } else {
+            mn[1] = -2.0 * divj / a.s[1];
+            mn[7] = -2.0 * (G[0][0] - G[1][1]) / (3.0 * snu);
+            mn[8] = -(G[1][0] + G[0][1]) / (3.0 * snu);
+        }
+    }
+    double Dk[Q], add[Q];
+    sfor<Q>([&](auto k) { Dk[k] = mn[k] * (1.0 / norm2<L>(CV(k))); });
+    back_transform<L, (1u << Q) - 1u>(Dk, add);
+    const double jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
+    const double jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
+    ST* __restrict__ buf = static_cast<ST*>(a.dst);
+    const int dims[3] = {nx, ny, nz};
+    const int pos[3] = {x, y, z};
+    sfor<Q>([&](auto i) {
+        constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+        const double w = L::w36(CV(i)) / 36.0;
+        const double cj = cx * j[0] + cy * j[1] + cz * j[2];
+        const double cF = cx * F[0] + cy * F[1] + cz * F[2];
+        const double feq = w * (dr + 3.0 * cj + 4.5 * cj * cj * ir0 - 1.5 * jj);
+        const double fb = w * (3.0 * cF - 3.0 * jF + 9.0 * cj * cF * ir0);
+        double v = feq + add[i] - 0.5 * fb;
+        // un-stream: write where the pull of (node, i) will read
+        int s[3];
+        int nout = 0, face = -1;
+        for (int ax = 0; ax < 3; ++ax) {
+            const int cax = ax == 0 ? cx : (ax == 1 ? cy : cz);
+            s[ax] = pos[ax] - cax;
+            if (cax == 0 || (s[ax] >= 0 && s[ax] < dims[ax])) continue;
+            const int fc = 2 * ax + (s[ax] < 0 ? 0 : 1);
+            if ((a.wall_mask >> fc) & 1) {
+                ++nout;
+                face = fc;
+            } else {
+                s[ax] = s[ax] < 0 ? s[ax] + dims[ax] : s[ax] - dims[ax];
+            }
+        }
+        if (nout == 0) {
+            Store<ST>::st(buf + CV(i) * a.stride + (s[2] * ny + s[1]) * nx + s[0], R(v));
+        } else {
+            if (nout == 1 && ((a.lid_mask >> face) & 1)) {
+                const double cu = cx * a.lid[face][0] + cy * a.lid[face][1] + cz * a.lid[face][2];
+                v -= 6.0 * w * r0 * cu;
+            }
+            Store<ST>::st(buf + opp<L>(CV(i)) * a.stride + node, R(v));
+        }
+    });
+}
+
+// ------------------------------------------------------------------------------------------
+// global sums in FP64: per-block partials into scratch, then one ordered final pass
+
+constexpr int SUM_THREADS = 256;
+
+template <class L, class ST>
+__global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename Store<ST>::R> a, double* __restrict__ partial) {
+    using R = typename Store<ST>::R;
+    constexpr int D = L::D;
+    const int N = a.nx * a.ny * a.nz;
+    double acc[1 + D];
+#pragma unroll
+    for (int c = 0; c <= D; ++c) acc[c] = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const int x = n % a.nx;
+        const int y = (n / a.nx) % a.ny;
+        const int z = n / (a.nx * a.ny);
+        R f[L::Q];
+        pull<L, ST, R>(a, x, y, z, f);
+        sfor<L::Q>([&](auto i) {
+            const double v = double(f[i]);
+            acc[0] += v;
+            sfor<D>([&](auto d) {
+                constexpr int cd = L::c(CV(i), CV(d));
+                if constexpr (cd == 1) acc[1 + CV(d)] += v;
+                if constexpr (cd == -1) acc[1 + CV(d)] -= v;
+            });
+        });
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const double Fd = a.force_field ? double(a.force_field[d * N + n]) : double(a.F[d]);
+            acc[1 + d] += 0.5 * Fd;
+        }
+    }
+    __shared__ double red[SUM_THREADS / 32][1 + D];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c <= D; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c <= D; ++c) {
+            double v = 0.0;
+            for (int w = 0; w < SUM_THREADS / 32; ++w) v += red[w][c];
+            partial[blockIdx.x * (1 + D) + c] = v;
+        }
+    }
+}
+
+// sums nblocks partial rows of width `width` in block order into out[width]
+__global__ void k_sums_final(const double* __restrict__ partial, int nblocks, int width, double* __restrict__ out);
+
+}  // namespace lbm

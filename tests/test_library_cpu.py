@@ -1,0 +1,97 @@
+"""The C-ABI library builds, loads and exports every call declared in include/lbm.h, and its
+host-side argument checks reject bad input without touching a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1704_07559_gb300 import build, lbm
+
+    build.build()
+    return lbm.lib()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(lbm_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_call(L):
+    names = header_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(L, name), name
+    from paper_1704_07559_gb300 import lbm
+
+    assert sorted(lbm.API) == names
+
+
+def test_default_params(L):
+    from paper_1704_07559_gb300 import lbm
+
+    p = lbm.default_params()
+    assert p.precision == 1 and p.closure == 0 and p.formula == 0
+    assert p.smag_iters == 6 and p.rho0 == 1.0 and list(p.bc) == [0] * 6
+
+
+D3 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1.6, 1.4, 1.6, 1.4, 1.6, 1.6, 1.6, 1.98, 1.98, 1.98]
+
+
+def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
+    from paper_1704_07559_gb300 import lbm
+
+    p = lbm.default_params()
+    if mutate:
+        mutate(p)
+    r = rates if rates is not None else (D3 if lattice == 19 else [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1.6, 1.6])
+    arr = (ctypes.c_double * len(r))(*r)
+    ctx = ctypes.c_void_p()
+    rc = L.lbm_create(ctypes.byref(ctx), lattice, dims[0], dims[1], dims[2], arr, None, ctypes.byref(p))
+    return rc, ctx
+
+
+@pytest.mark.parametrize("case", [
+    dict(lattice=7),
+    dict(dims=(0, 8, 8)),
+    dict(lattice=9, dims=(8, 8, 2)),
+    dict(dims=(8, 70000, 1)),
+    dict(dims=(2048, 2048, 1024)),
+    dict(rates=D3[:3] + [0.1] + D3[4:]),                       # nonzero conserved rate
+    dict(rates=D3[:1] + [2.5] + D3[2:]),                       # rate outside (0, 2)
+    dict(rates=D3[:13] + [1.2] + D3[14:]),                     # split viscous rates with Yu
+    dict(mutate=lambda p: setattr(p, "precision", 9)),
+    dict(mutate=lambda p: setattr(p, "closure", 5)),
+    dict(mutate=lambda p: setattr(p, "formula", 2)),
+    dict(mutate=lambda p: p.bc.__setitem__(0, 1)),             # -x wall with +x periodic
+    dict(mutate=lambda p: setattr(p, "rho0", 0.0)),
+    dict(mutate=lambda p: setattr(p, "smag_iters", 0)),
+    dict(mutate=lambda p: (setattr(p, "precision", 2), setattr(p, "closure", 2))),
+    dict(lattice=9, mutate=lambda p: setattr(p, "precision", 2)),
+    dict(mutate=lambda p: (setattr(p, "closure", 2), setattr(p, "pl_tau_min", 0.5))),
+])
+def test_create_rejects_bad_arguments(L, case):
+    rc, ctx = create(L, **case)
+    assert rc == -1
+    assert ctx.value is None
+    assert L.lbm_last_error(None).startswith(b"lbm_create: invalid")
+
+
+def test_chai_accepts_split_viscous_rates_host_checks(L):
+    """Chai's formula uses each viscous rate on its own, so split rates pass the host checks
+    (the call then needs a GPU for its scratch; without one it reports a CUDA error)."""
+    rc, ctx = create(L, rates=D3[:13] + [1.2] + D3[14:], mutate=lambda p: setattr(p, "formula", 1))
+    assert rc in (0, -2, -3)
+    if rc == 0:
+        L.lbm_destroy(ctx)
+
+
+def test_null_context_calls_fail_cleanly(L):
+    assert L.lbm_step(None, 1) == -1
+    assert L.lbm_destroy(None) == 0
+    assert L.lbm_layout(None, None, None, None) == -1
