@@ -7,7 +7,11 @@ moments, strain rate, closure, relaxation, force, store).  The metric is MLUPS (
 node updates per second) and the fraction of the measured HBM bandwidth that the minimum
 traffic (19 populations read + 19 written, 152 bytes per node update) represents.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-variants]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|fp16s|bf16s|fp64] [--formula yu|chai] [--no-variants] [--quick]
+
+--precision / --formula pick the headline (default fp32 / yu); --quick skips the end-to-end
+run, the other variants and the CPU baseline (used for profiler captures).
 
 With N > 1 (torchrun) every rank runs its own replica of the workload (the step has no
 cross-GPU exchange), value = all ranks' node updates / the slowest rank's time.
@@ -34,6 +38,9 @@ RATES = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / TAU0, 1.4, 1 / TAU0, 1.4, 1 /
          1.98, 1.98]
 BC = ["periodic", "periodic", "wall", "wall", "periodic", "periodic"]
 BYTES_PER_LUP = {"fp32": 152, "fp64": 304, "fp16s": 76, "bf16s": 76}
+STORAGE_NOTE = {"fp32": "fp32 populations, fp32 arithmetic", "fp64": "fp64 populations, fp64 arithmetic",
+                "fp16s": "fp16 populations (delta-rho form), fp32 arithmetic",
+                "bf16s": "bf16 populations (delta-rho form), fp32 arithmetic"}
 WORKLOAD = "D3Q19 MRT Smagorinsky LES channel 256x128x128, walls at y, g_x=1e-6, Cs=0.17, tau0=0.51"
 METRIC = "MLUPS, MRT step + strain rate (Smagorinsky LES channel)"
 
@@ -213,7 +220,7 @@ def run_ours(args):
 
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    lat = make_lattice("fp32", "yu")
+    lat = make_lattice(args.precision, args.formula)
     N = lat.N
 
     # timed region: barrier + synchronize on both sides, max over ranks
@@ -237,24 +244,27 @@ def run_ours(args):
     # kernel duration per launch for the roofline (events around each launch)
     per = time_steps(lat, min(args.steps, 500), 0, per_launch=True)
     k_ms = statistics.mean(per)
-    achieved = BYTES_PER_LUP["fp32"] * N / (k_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_LUP[args.precision] * N / (k_ms * 1e-3) / 1e9
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": [NX, NY, NZ], "formula": "yu",
-                   "closure": "smagorinsky", "precision": "fp32 populations, fp32 arithmetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": [NX, NY, NZ], "formula": args.formula,
+                   "closure": "smagorinsky", "precision": STORAGE_NOTE[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (two 319 MB population buffers per step)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_step<D3Q19,float,SMAG,YU,force>", "bytes_per_lup": BYTES_PER_LUP["fp32"],
+                     "kernel": "k_step<D3Q19,%s,SMAG,%s,force>" % (args.precision, args.formula.upper()),
+                     "bytes_per_lup": BYTES_PER_LUP[args.precision],
                      "kernel_ms": round(k_ms, 5)},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
-    if rank == 0:
+    if rank == 0 and args.quick:
+        print(json.dumps(out), flush=True)
+    elif rank == 0:
         # end to end through the C ABI with host buffers
         e2e_s, h2d, d2h = time_e2e(lat, max(3, min(args.steps, 50)))
         out["e2e"] = {"value": round(world * N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
@@ -345,7 +355,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16s", "bf16s", "fp64"])
+    ap.add_argument("--formula", default="yu", choices=["yu", "chai"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

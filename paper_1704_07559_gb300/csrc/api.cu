@@ -100,6 +100,18 @@ void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
     a->force_field = c->p.force_field ? static_cast<const R*>(c->force_field) : nullptr;
 }
 
+// source / destination buffers and their per-population base pointers
+template <class R>
+void set_buffers(const lbm_ctx* c, lbm::StepArgs<R>* a, const void* src, void* dst) {
+    a->src = src;
+    a->dst = dst;
+    const size_t pitch = (size_t)c->stride * c->elem_bytes;
+    for (int i = 0; i < 19; ++i) {
+        a->srcp[i] = (src && i < c->q) ? static_cast<const char*>(src) + i * pitch : nullptr;
+        a->dstp[i] = (dst && i < c->q) ? static_cast<char*>(dst) + i * pitch : nullptr;
+    }
+}
+
 bool has_force(const lbm_ctx* c) {
     return c->p.force_field || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
 }
@@ -132,8 +144,7 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
         lbm::StepArgs<double> a;
         fill_args(c, &a);
         a.readout = readout;
-        a.src = src;
-        a.dst = dst;
+        set_buffers(c, &a, src, dst);
         a.S_out = static_cast<double*>(S);
         a.tau_out = static_cast<double*>(tau);
         a.drho_out = static_cast<double*>(drho);
@@ -144,8 +155,7 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
     lbm::StepArgs<float> a;
     fill_args(c, &a);
     a.readout = readout;
-    a.src = src;
-    a.dst = dst;
+    set_buffers(c, &a, src, dst);
     a.S_out = static_cast<float*>(S);
     a.tau_out = static_cast<float*>(tau);
     a.drho_out = static_cast<float*>(drho);
@@ -169,12 +179,21 @@ int check_bound(lbm_ctx* c) {
 
 namespace lbm {
 __global__ void k_sums_final(const double* __restrict__ partial, int nblocks, int width, double* __restrict__ out) {
-    // one warp: lane c sums column c in block order (deterministic)
-    const int c = threadIdx.x;
-    if (c >= width) return;
-    double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) v += partial[b * width + c];
-    out[c] = v;
+    // one block of 256 threads: thread t adds rows t, t + 256, ... of each column, then a fixed
+    // shared-memory tree (the order never changes, so the result is reproducible)
+    __shared__ double red[256];
+    for (int c = 0; c < width; ++c) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[b * width + c];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = red[0];
+        __syncthreads();
+    }
 }
 }  // namespace lbm
 
@@ -329,7 +348,7 @@ int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad
     if (!drho || !u) return fail(c, LBM_ERR_ARG, "lbm_init: drho and u are required");
     lbm::StepArgs<double> a;
     fill_args(c, &a);
-    a.dst = c->buf[c->cur];
+    set_buffers(c, &a, nullptr, c->buf[c->cur]);
     cudaError_t e;
     const Tag t = tag_of(c->q, c->p.precision);
     switch (t) {
@@ -399,13 +418,13 @@ int lbm_sums(lbm_ctx* c, double* out) {
     if (c->p.precision == LBM_FP64) {
         lbm::StepArgs<double> a;
         fill_args(c, &a);
-        a.src = c->buf[c->cur];
+        set_buffers(c, &a, c->buf[c->cur], nullptr);
         e = t == T_D3Q19_F64 ? lbm::sums_d3q19_f64(a, c->partial, c->result, c->stream)
                              : lbm::sums_d2q9_f64(a, c->partial, c->result, c->stream);
     } else {
         lbm::StepArgs<float> a;
         fill_args(c, &a);
-        a.src = c->buf[c->cur];
+        set_buffers(c, &a, c->buf[c->cur], nullptr);
         switch (t) {
             case T_D3Q19_F32: e = lbm::sums_d3q19_f32(a, c->partial, c->result, c->stream); break;
             case T_D3Q19_F16: e = lbm::sums_d3q19_f16(a, c->partial, c->result, c->stream); break;

@@ -53,7 +53,7 @@ cudaError_t launch_sums(const StepArgs<typename Store<ST>::R>& a, double* partia
     k_sums<L, ST><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(a, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sums_final<<<1, 32, 0, s>>>(partial, SUM_BLOCKS, 1 + L::D, out);
+    k_sums_final<<<1, 256, 0, s>>>(partial, SUM_BLOCKS, 1 + L::D, out);
     return cudaGetLastError();
 }
 

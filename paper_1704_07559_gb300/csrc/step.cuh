@@ -103,6 +103,14 @@ __device__ __forceinline__ float r_pow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double r_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float r_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double r_abs(double x) { return fabs(x); }
+// Closure arithmetic: in FP32 the fast reciprocal / reciprocal-square-root / power intrinsics
+// (errors of a few ulp, far inside the FP32 tolerance of S); in FP64 the IEEE operations.
+__device__ __forceinline__ float c_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double c_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float c_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double c_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float c_pow(float x, float y) { return y == 0.0f ? 1.0f : __powf(x, y); }
+__device__ __forceinline__ double c_pow(double x, double y) { return pow(x, y); }
 
 // ------------------------------------------------------------------------------------------
 // kernel arguments (by value)
@@ -114,6 +122,8 @@ struct StepArgs {
     long long stride;     // elements between population arrays
     const void* src;      // post-collision buffer of the previous step
     void* dst;            // post-collision buffer of this step
+    const void* srcp[19]; // src + i * stride, population i (filled on the host)
+    void* dstp[19];       // dst + i * stride
     const R* force_field; // d x N, or nullptr for the uniform force F
     R F[3];
     R s[19];              // relaxation rates; the viscous entries hold 1/tau0
@@ -205,6 +215,135 @@ __host__ __device__ constexpr uint32_t mask_viscous() {
         if (L::viscous(k)) m |= 1u << k;
     return m;
 }
+template <class L>
+__host__ __device__ constexpr uint32_t mask_all_but_density() {
+    return ((1u << L::Q) - 1u) & ~1u;
+}
+
+// Forward and backward transforms.  The generic form (any lattice) sums the nonzero entries of
+// each row of T over the opposite-pair sums and differences.  D3Q19 has a hand-factored form
+// that shares the axis / edge partial sums between rows; it computes the same linear maps.
+template <class L>
+struct Xf {
+    // m[k] = (T f)_k for every k (m[0] = drho, m[3], m[5], m[7] = raw momentum)
+    template <class R>
+    static __device__ __forceinline__ void forward(R f0, const R (&P)[L::NP], const R (&Dd)[L::NP], R (&m)[L::Q]) {
+        sfor<L::Q>([&](auto k) { m[k] = moment<L, CV(k)>(f0, P, Dd); });
+    }
+    template <uint32_t USE, class R>
+    static __device__ __forceinline__ void backward(const R (&D)[L::Q], R (&out)[L::Q]) {
+        back_transform<L, USE>(D, out);
+    }
+};
+
+template <>
+struct Xf<D3Q19> {
+    // pair order: x (1,2), y (3,4), z (5,6), (7,10), (8,9), (11,14), (12,13), (15,18), (16,17)
+    template <class R>
+    static __device__ __forceinline__ void forward(R f0, const R (&P)[9], const R (&D)[9], R (&m)[19]) {
+        const R Exy = P[3] + P[4], Exz = P[5] + P[6], Eyz = P[7] + P[8];
+        const R Pyz = P[1] + P[2];
+        const R Sax = P[0] + Pyz;
+        const R Q = Exy + Exz;
+        const R Sed = Q + Eyz;
+        m[0] = f0 + Sax + Sed;
+        const R Ex = (D[3] - D[4]) + (D[5] - D[6]);
+        const R Ey = (D[3] + D[4]) + (D[7] - D[8]);
+        const R Ez = (D[5] + D[6]) + (D[7] + D[8]);
+        m[3] = D[0] + Ex;
+        m[5] = D[1] + Ey;
+        m[7] = D[2] + Ez;
+        m[4] = fma(R(-4), D[0], Ex);
+        m[6] = fma(R(-4), D[1], Ey);
+        m[8] = fma(R(-4), D[2], Ez);
+        m[1] = fma(R(8), Sed, fma(R(-11), Sax, R(-30) * f0));
+        m[2] = fma(R(-4), Sax, fma(R(12), f0, Sed));
+        const R Qm = fma(R(-2), Eyz, Q);
+        m[9] = fma(R(2), P[0], Qm - Pyz);
+        m[10] = fma(R(-4), P[0], fma(R(2), Pyz, Qm));
+        const R dyz = P[1] - P[2], dxyz = Exy - Exz;
+        m[11] = dyz + dxyz;
+        m[12] = fma(R(-2), dyz, dxyz);
+        m[13] = P[3] - P[4];
+        m[14] = P[7] - P[8];
+        m[15] = P[5] - P[6];
+        m[16] = (D[3] - D[4]) - (D[5] - D[6]);
+        m[17] = (D[7] - D[8]) - (D[3] + D[4]);
+        m[18] = (D[5] + D[6]) - (D[7] + D[8]);
+    }
+
+    // out_i = sum_k T_ki a_k.  The factored form needs every non-conserved a_k; with CONS the
+    // momentum entries a_3, a_5, a_7 are included too (a_0 is always absent).  Other masks use
+    // the generic form.
+    template <uint32_t USE, class R>
+    static __device__ __forceinline__ void backward(const R (&a)[19], R (&out)[19]) {
+        constexpr uint32_t NC = mask_nonconserved<D3Q19>();
+        if constexpr (USE != NC && USE != mask_all_but_density<D3Q19>()) {
+            back_transform<D3Q19, USE>(a, out);
+        } else {
+            constexpr bool CONS = (USE >> 3) & 1u;
+            out[0] = fma(R(12), a[2], R(-30) * a[1]);
+            // axis populations
+            const R B1 = fma(R(-4), a[2], R(-11) * a[1]);
+            const R C = fma(R(2), a[10], -a[9]);
+            const R W = fma(R(-2), a[12], a[11]);
+            const R Ex = fma(R(-2), C, B1);
+            const R Ey = B1 + C + W;
+            const R Ez = B1 + C - W;
+            R Ox = R(-4) * a[4], Oy = R(-4) * a[6], Oz = R(-4) * a[8];
+            if constexpr (CONS) {
+                Ox += a[3];
+                Oy += a[5];
+                Oz += a[7];
+            }
+            out[1] = Ex + Ox;
+            out[2] = Ex - Ox;
+            out[3] = Ey + Oy;
+            out[4] = Ey - Oy;
+            out[5] = Ez + Oz;
+            out[6] = Ez - Oz;
+            // edge populations
+            const R B2 = fma(R(8), a[1], a[2]);
+            const R G = a[9] + a[10], H = a[11] + a[12];
+            R X = a[4], Y = a[6], Z = a[8];
+            if constexpr (CONS) {
+                X += a[3];
+                Y += a[5];
+                Z += a[7];
+            }
+            {  // xy edges: (7,10) and (8,9)
+                const R base = B2 + G + H;
+                const R E4 = base + a[13], E5 = base - a[13];
+                const R u = X + a[16], v = Y - a[17];
+                const R O4 = v + u, O5 = v - u;
+                out[7] = E4 + O4;
+                out[10] = E4 - O4;
+                out[8] = E5 + O5;
+                out[9] = E5 - O5;
+            }
+            {  // xz edges: (11,14) and (12,13)
+                const R base = B2 + G - H;
+                const R E6 = base + a[15], E7 = base - a[15];
+                const R u = X - a[16], v = Z + a[18];
+                const R O6 = v + u, O7 = v - u;
+                out[11] = E6 + O6;
+                out[14] = E6 - O6;
+                out[12] = E7 + O7;
+                out[13] = E7 - O7;
+            }
+            {  // yz edges: (15,18) and (16,17)
+                const R base = fma(R(-2), G, B2);
+                const R E8 = base + a[14], E9 = base - a[14];
+                const R u = Y + a[17], v = Z - a[18];
+                const R O8 = v + u, O9 = v - u;
+                out[15] = E8 + O8;
+                out[18] = E8 - O8;
+                out[16] = E9 + O9;
+                out[17] = E9 - O9;
+            }
+        }
+    }
+};
 
 // N_c = sum_i c_ia c_ib v_i for each strain component c = (a, b)
 template <class L, class R>
@@ -272,6 +411,8 @@ struct Eq<D3Q19> {
         t[17] = R(0);
         t[18] = R(0);
     }
+    // moments with identically zero equilibrium and force parts (ghost moments t_x, t_y, t_z)
+    static __host__ __device__ constexpr bool ghost(int k) { return k >= 16; }
     // Yu formula eq. (LuoS) split as S = A + s_nu B (A: the s1 m1 part)
     template <class R>
     static __device__ __forceinline__ void yu_split(const R (&mn)[19], R s1, R ir0, R (&A)[6], R (&B)[6]) {
@@ -283,8 +424,8 @@ struct Eq<D3Q19> {
         A[4] = R(0);
         A[5] = R(0);
         B[0] = R(-0.5) * ir0 * mn[9];
-        B[1] = R(0.25) * ir0 * (mn[9] - R(3) * mn[11]);
-        B[2] = R(0.25) * ir0 * (mn[9] + R(3) * mn[11]);
+        B[1] = R(0.25) * ir0 * fma(R(-3), mn[11], mn[9]);
+        B[2] = R(0.25) * ir0 * fma(R(3), mn[11], mn[9]);
         B[3] = R(-1.5) * ir0 * mn[13];
         B[4] = R(-1.5) * ir0 * mn[14];
         B[5] = R(-1.5) * ir0 * mn[15];
@@ -319,6 +460,7 @@ struct Eq<D2Q9> {
         t[7] = R(2) * (j[0] * F[0] - j[1] * F[1]) * ir0;
         t[8] = (j[0] * F[1] + j[1] * F[0]) * ir0;
     }
+    static __host__ __device__ constexpr bool ghost(int) { return false; }
     // Yu-type D2Q9 formula (Sec. 5.4 procedure): S_xx,yy = -(s_e m_e +- 3 s_nu m_pxx)/(4 rho0),
     // S_xy = -3 s_nu m_pxy / (2 rho0)
     template <class R>
@@ -333,17 +475,54 @@ struct Eq<D2Q9> {
     }
 };
 
+// He-Luo equilibrium (eq. (edf), delta-rho form) and the discrete force in opposite-pair form:
+// Pe_p = feq_a + feq_b = 2 w (drho + 4.5 (c.j)^2/rho0 - 1.5 j.j/rho0), De_p = feq_a - feq_b =
+// 6 w c.j;  PF_p = Fbar_a + Fbar_b = 2 w (9 (c.j)(c.F) - 3 j.F)/rho0, DF_p = 6 w c.F;
+// rest: fe0 = w0 (drho - 1.5 j.j/rho0), F0 = -3 w0 j.F/rho0.  (c = c_a, w = w_a.)
+template <class L, bool FORCE, class R>
+__device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const R (&F)[3], R ir0, R& fe0,
+                                                  R (&Pe)[L::NP], R (&De)[L::NP], R& F0, R (&PF)[L::NP],
+                                                  R (&DF)[L::NP]) {
+    const R jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
+    const R base = fma(R(-1.5), jj, drho);
+    constexpr R w0 = R(L::w36(0) / 36.0);
+    fe0 = w0 * base;
+    R jF = R(0);
+    if constexpr (FORCE) {
+        jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
+        F0 = R(-3) * w0 * jF;
+    } else {
+        F0 = R(0);
+    }
+    sfor<L::NP>([&](auto p) {
+        constexpr int i = L::pa(CV(p));
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        constexpr R w = R(L::w36(i) / 36.0);
+        const R cj = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), j[0]), j[1]), j[2]);
+        Pe[p] = (R(2) * w) * fma(R(4.5) * cj, cj * ir0, base);
+        De[p] = (R(6) * w) * cj;
+        if constexpr (FORCE) {
+            const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
+            PF[p] = (R(2) * w) * fma(R(9) * cj, cF * ir0, R(-3) * jF);
+            DF[p] = (R(6) * w) * cF;
+        } else {
+            PF[p] = R(0);
+            DF[p] = R(0);
+        }
+    });
+}
+
 // ------------------------------------------------------------------------------------------
 // closure: solve tau with S = A + (1/tau) B
 
 template <class L, class R>
-__device__ __forceinline__ R strain_norm(const R (&S)[L::NS]) {
-    R ss;
+__device__ __forceinline__ R strain_dot(const R (&S)[L::NS], const R (&T)[L::NS]) {
+    // S:T with the off-diagonal components counted twice
     if constexpr (L::NS == 6)
-        ss = S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + R(2) * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]);
+        return fma(S[0], T[0], fma(S[1], T[1], S[2] * T[2])) +
+               R(2) * fma(S[3], T[3], fma(S[4], T[4], S[5] * T[5]));
     else
-        ss = S[0] * S[0] + S[1] * S[1] + R(2) * S[2] * S[2];
-    return r_sqrt(R(2) * ss);
+        return fma(S[0], T[0], S[1] * T[1]) + R(2) * S[2] * T[2];
 }
 
 template <class L, class R>
@@ -352,34 +531,40 @@ __device__ __forceinline__ void affine(const R (&A)[L::NS], const R (&B)[L::NS],
     for (int c = 0; c < L::NS; ++c) S[c] = fma(s, B[c], A[c]);
 }
 
-// returns tau; S holds the strain rate at the returned tau
+// Returns tau and leaves S = A + B/tau.  |S|^2 = 2 S:S = 2 (a + 2 b s + c s^2) with a = A:A,
+// b = A:B, c = B:B is the exact quadratic in s = 1/tau, so each fixed-point sweep costs a
+// reciprocal, two FMAs and a square root.  Smagorinsky: `smag_iters` sweeps from tau0, stopping
+// early only when a sweep returns its input bit for bit (every later sweep would too).  Power
+// law: sweeps until |tau_new - tau| <= pl_tol tau_new or pl_max_iter sweeps.
 template <class L, class R, int CLOSURE>
 __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS], const StepArgs<R>& a,
-                                       R (&S)[L::NS]) {
+                                       R (&S)[L::NS], R& snu) {
     if constexpr (CLOSURE == CL_NEWTON) {
-        affine<L>(A, B, a.s[L::NU0], S);
+        snu = a.s[L::NU0];
+        affine<L>(A, B, snu, S);
         return a.tau0;
-    } else if constexpr (CLOSURE == CL_SMAG) {
-        R tau = a.tau0;
-        for (int it = 0; it < a.smag_iters; ++it) {
-            affine<L>(A, B, R(1) / tau, S);
-            tau = fma(a.smag_c3, strain_norm<L>(S), a.tau0);
-        }
-        affine<L>(A, B, R(1) / tau, S);
-        return tau;
     } else {
+        const R qa = strain_dot<L>(A, A), qb2 = R(2) * strain_dot<L>(A, B), qc = strain_dot<L>(B, B);
+        auto gnorm = [&](R s) { return c_sqrt(R(2) * fma(fma(qc, s, qb2), s, qa)); };
         R tau = a.tau0;
-        for (int it = 1; it <= a.pl_max_iter; ++it) {
-            affine<L>(A, B, R(1) / tau, S);
-            const R g = strain_norm<L>(S);
-            R tn = fma(a.pl_k3, r_pow(g, a.pl_nm1), R(0.5));
-            if (!(tn >= a.pl_tau_min)) tn = a.pl_tau_min;
-            if (tn > a.pl_tau_max) tn = a.pl_tau_max;
-            const R diff = r_abs(tn - tau);
-            tau = tn;
-            if (diff <= a.pl_tol * tn) break;
+        if constexpr (CLOSURE == CL_SMAG) {
+            for (int it = 0; it < a.smag_iters; ++it) {
+                const R tn = fma(a.smag_c3, gnorm(c_rcp(tau)), a.tau0);
+                if (tn == tau) break;
+                tau = tn;
+            }
+        } else {
+            for (int it = 1; it <= a.pl_max_iter; ++it) {
+                R tn = fma(a.pl_k3, c_pow(gnorm(c_rcp(tau)), a.pl_nm1), R(0.5));
+                if (!(tn >= a.pl_tau_min)) tn = a.pl_tau_min;
+                if (tn > a.pl_tau_max) tn = a.pl_tau_max;
+                const R diff = r_abs(tn - tau);
+                tau = tn;
+                if (diff <= a.pl_tol * tn) break;
+            }
         }
-        affine<L>(A, B, R(1) / tau, S);
+        snu = c_rcp(tau);
+        affine<L>(A, B, snu, S);
         return tau;
     }
 }
@@ -388,27 +573,26 @@ __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS],
 // pull streaming
 
 // Pre-collision populations of node (x,y,z).  Interior rows (y, z away from the faces, and x
-// away from non-periodic x faces) use wrapped x neighbours and direct row offsets; other nodes
-// take the general rule: periodic faces wrap, a population whose source lies behind a wall is
-// reflected from the opposite population of the same node, plus the moving-wall term when it
-// crosses exactly one moving face.
+// away from non-periodic x faces) read population i at node + (x wrap) - c_iy nx - c_iz nx ny,
+// the last two terms being the same for the whole warp; other nodes take the general rule:
+// periodic faces wrap, a population whose source lies behind a wall is reflected from the
+// opposite population of the same node, plus the moving-wall term when it crosses exactly one
+// moving face.
 template <class L, class ST, class R>
 __device__ __forceinline__ void pull(const StepArgs<R>& a, int x, int y, int z, R (&f)[L::Q]) {
-    const ST* __restrict__ src = static_cast<const ST*>(a.src);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long st = a.stride;
-    const int node = (z * ny + y) * nx + x;
-    const int xm = x == 0 ? nx - 1 : x - 1;
-    const int xp = x == nx - 1 ? 0 : x + 1;
+    const int nxy = nx * ny;
+    const int node = z * nxy + y * nx + x;
     const bool xwall = (a.wall_mask & 3) != 0;
     bool fast = y > 0 && y < ny - 1 && (!xwall || (x > 0 && x < nx - 1));
     if constexpr (L::D == 3) fast = fast && z > 0 && z < nz - 1;
     if (fast) {
+        const int dxm = x == 0 ? nx - 1 : -1;       // source of c_x = +1: x - 1 (wrapped)
+        const int dxp = x == nx - 1 ? 1 - nx : 1;   // source of c_x = -1: x + 1 (wrapped)
         sfor<L::Q>([&](auto i) {
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
-            const int sx = cx == 0 ? x : (cx > 0 ? xm : xp);
-            const int row = ((z - cz) * ny + (y - cy)) * nx;
-            f[i] = Store<ST>::ld(src + CV(i) * st + row + sx);
+            const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) - (cy * nx + cz * nxy);
+            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
         });
         return;
     }
@@ -433,9 +617,9 @@ __device__ __forceinline__ void pull(const StepArgs<R>& a, int x, int y, int z, 
             }
         });
         if (nout == 0) {
-            f[i] = Store<ST>::ld(src + CV(i) * st + (s[2] * ny + s[1]) * nx + s[0]);
+            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + (s[2] * ny + s[1]) * nx + s[0]);
         } else {
-            R v = Store<ST>::ld(src + opp<L>(CV(i)) * st + node);
+            R v = Store<ST>::ld(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + node);
             if (nout == 1 && ((a.lid_mask >> face) & 1)) {
                 const R cu = R(L::c(CV(i), 0)) * a.lid[face][0] + R(L::c(CV(i), 1)) * a.lid[face][1] +
                              R(L::c(CV(i), 2)) * a.lid[face][2];
@@ -463,14 +647,11 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
     R f[Q];
     pull<L, ST, R>(a, x, y, z, f);
 
-    // macroscopic: drho = sum f, j = sum c f + F/2 (from opposite-pair sums and differences)
     R P[NP], Dd[NP];
     sfor<NP>([&](auto p) {
         P[p] = f[L::pa(CV(p))] + f[L::pb(CV(p))];
         Dd[p] = f[L::pa(CV(p))] - f[L::pb(CV(p))];
     });
-    R drho = f[0];
-    sfor<NP>([&](auto p) { drho += P[p]; });
     R F[3] = {R(0), R(0), R(0)};
     if constexpr (FORCE) {
         if (a.force_field) {
@@ -479,94 +660,77 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
             sfor<L::D>([&](auto d) { F[d] = a.F[d]; });
         }
     }
-    R j[3] = {R(0), R(0), R(0)};
-    sfor<L::D>([&](auto d) {
-        R acc = nzero<R>();
-        sfor<NP>([&](auto p) { acc = cadd<L::c(L::pa(CV(p)), CV(d))>(acc, Dd[p]); });
-        j[d] = FORCE ? fma(R(0.5), F[d], acc) : acc;
-    });
     const R ir0 = a.inv_rho0;
-
-    R S[NS];
-    R tau;
+    R drho, j[3] = {R(0), R(0), R(0)};
+    R S[NS], tau, snu;
     R out[Q];  // f*_i = f_i - out_i
 
     if constexpr (FORMULA == F_YU) {
+        // Yu route: moments of f, closed-form equilibrium moments, S from six of them
+        R m[Q];
+        Xf<L>::forward(f[0], P, Dd, m);
+        drho = m[0];
+        j[0] = FORCE ? fma(R(0.5), F[0], m[3]) : m[3];
+        j[1] = FORCE ? fma(R(0.5), F[1], m[5]) : m[5];
+        if constexpr (L::D == 3) j[2] = FORCE ? fma(R(0.5), F[2], m[7]) : m[7];
         R meq[Q], TF[Q], mn[Q];
         Eq<L>::meq(drho, j, ir0, meq);
         if constexpr (FORCE) Eq<L>::tforce(j, F, ir0, TF);
         sfor<Q>([&](auto k) {
-            if constexpr (L::conserved(CV(k))) {
+            if constexpr (L::conserved(CV(k)))
                 mn[k] = R(0);
-            } else {
-                const R m = moment<L, CV(k)>(f[0], P, Dd);
-                if constexpr (FORCE)
-                    mn[k] = fma(R(0.5), TF[k], m - meq[k]);
-                else
-                    mn[k] = m - meq[k];
-            }
+            else if constexpr (Eq<L>::ghost(CV(k)))
+                mn[k] = m[k];
+            else if constexpr (FORCE)
+                mn[k] = fma(R(0.5), TF[k], m[k] - meq[k]);
+            else
+                mn[k] = m[k] - meq[k];
         });
         R A[NS], B[NS];
         Eq<L>::yu_split(mn, a.s[1], ir0, A, B);
-        tau = solve_tau<L, R, CLOSURE>(A, B, a, S);
+        tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
         if (a.readout) goto readout;
         {
-            const R snu = CLOSURE == CL_NEWTON ? a.s[L::NU0] : R(1) / tau;
             R Dk[Q];
             sfor<Q>([&](auto k) {
                 constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
                 if constexpr (L::conserved(CV(k))) {
                     if constexpr (FORCE)
-                        Dk[k] = -TF[k] * inv_n;
+                        Dk[k] = R(-inv_n) * TF[k];
                     else
                         Dk[k] = R(0);
                 } else {
-                    const R sk = L::viscous(CV(k)) ? snu : a.s[k];
-                    if constexpr (FORCE)
-                        Dk[k] = fma(sk, mn[k], -TF[k]) * inv_n;
+                    const R sk = (L::viscous(CV(k)) ? snu : a.s[k]) * inv_n;
+                    if constexpr (FORCE && !Eq<L>::ghost(CV(k)))
+                        Dk[k] = fma(sk, mn[k], R(-inv_n) * TF[k]);
                     else
-                        Dk[k] = sk * mn[k] * inv_n;
+                        Dk[k] = sk * mn[k];
                 }
             });
-            // with a force, the conserved moments 3, 5, 7 (D2Q9: 3, 5) carry -TF_k; TF_0 = 0
-            constexpr uint32_t use = FORCE ? (((1u << Q) - 1u) & ~1u) : mask_nonconserved<L>();
-            back_transform<L, use>(Dk, out);
+            Xf<L>::template backward<FORCE ? mask_all_but_density<L>() : mask_nonconserved<L>()>(Dk, out);
         }
     } else {
-        // Chai route: non-equilibrium distributions, collision operator applied to them
-        R fneq[Q], g[Q];  // g_i = Fbar_i (kept for the collision)
-        {
-            const R jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
-            const R jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
-            sfor<Q>([&](auto i) {
-                constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
-                constexpr R w = R(L::w36(CV(i)) / 36.0);
-                const R cj = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), j[0]), j[1]), j[2]);
-                const R feq = w * (drho + R(3) * cj + (R(4.5) * cj * cj) * ir0 - R(1.5) * jj);
-                if constexpr (FORCE) {
-                    const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
-                    const R fb = w * (R(3) * cF - R(3) * jF + (R(9) * cj * cF) * ir0);
-                    fneq[i] = fma(R(0.5), fb, f[i] - feq);
-                    g[i] = fb;
-                } else {
-                    fneq[i] = f[i] - feq;
-                    g[i] = R(0);
-                }
-            });
-        }
-        R Pn[NP], Dn[NP];
+        // Chai route: non-equilibrium distributions f - f_eq + Fbar/2 (in opposite-pair form), the
+        // collision operator T^-1 L T applied to them, and the second velocity moment of the result
+        drho = f[0];
+        sfor<NP>([&](auto p) { drho += P[p]; });
+        sfor<L::D>([&](auto d) {
+            R acc = nzero<R>();
+            sfor<NP>([&](auto p) { acc = cadd<L::c(L::pa(CV(p)), CV(d))>(acc, Dd[p]); });
+            j[d] = FORCE ? fma(R(0.5), F[d], acc) : acc;
+        });
+        R fe0, Pe[NP], De[NP], F0, PF[NP], DF[NP];
+        equilibrium_pairs<L, FORCE>(drho, j, F, ir0, fe0, Pe, De, F0, PF, DF);
+        R fn0 = f[0] - fe0, Pn[NP], Dn[NP];
+        if constexpr (FORCE) fn0 = fma(R(0.5), F0, fn0);
         sfor<NP>([&](auto p) {
-            Pn[p] = fneq[L::pa(CV(p))] + fneq[L::pb(CV(p))];
-            Dn[p] = fneq[L::pa(CV(p))] - fneq[L::pb(CV(p))];
+            Pn[p] = FORCE ? fma(R(0.5), PF[p], P[p] - Pe[p]) : P[p] - Pe[p];
+            Dn[p] = FORCE ? fma(R(0.5), DF[p], Dd[p] - De[p]) : Dd[p] - De[p];
         });
         R mn[Q];
-        sfor<Q>([&](auto k) {
-            if constexpr (L::conserved(CV(k)))
-                mn[k] = R(0);
-            else
-                mn[k] = moment<L, CV(k)>(fneq[0], Pn, Dn);
-        });
+        Xf<L>::forward(fn0, Pn, Dn, mn);
         const R kS = R(-1.5) * ir0;  // S = -N / (2 rho0 cs2)
+        R Om[Q];                     // Omega (Newtonian) or its rate-independent part
         if constexpr (CLOSURE == CL_NEWTON) {
             R Dk[Q];
             sfor<Q>([&](auto k) {
@@ -574,18 +738,17 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
                 if constexpr (L::conserved(CV(k)))
                     Dk[k] = R(0);
                 else
-                    Dk[k] = a.s[k] * mn[k] * inv_n;
+                    Dk[k] = (a.s[k] * inv_n) * mn[k];
             });
-            R Om[Q];
-            back_transform<L, mask_nonconserved<L>()>(Dk, Om);
+            Xf<L>::template backward<mask_nonconserved<L>()>(Dk, Om);
             R N[NS];
             contract<L>(Om, N);
 #pragma unroll
             for (int c = 0; c < NS; ++c) S[c] = kS * N[c];
             tau = a.tau0;
+            snu = a.s[L::NU0];
             if (a.readout) goto readout;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) out[i] = Om[i] - g[i];
+            sfor<Q>([&](auto i) { out[i] = Om[i]; });
         } else {
             R Df[Q], Dv[Q];
             sfor<Q>([&](auto k) {
@@ -593,35 +756,37 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
                 if constexpr (L::conserved(CV(k)) || L::viscous(CV(k)))
                     Df[k] = R(0);
                 else
-                    Df[k] = a.s[k] * mn[k] * inv_n;
+                    Df[k] = (a.s[k] * inv_n) * mn[k];
                 if constexpr (L::viscous(CV(k)))
-                    Dv[k] = mn[k] * inv_n;
+                    Dv[k] = inv_n * mn[k];
                 else
                     Dv[k] = R(0);
             });
-            R Of[Q], Ov[Q];
-            back_transform<L, mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Of);
-            back_transform<L, mask_viscous<L>()>(Dv, Ov);
+            R Ov[Q];
+            Xf<L>::template backward<mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Om);
+            Xf<L>::template backward<mask_viscous<L>()>(Dv, Ov);
             R Nf[NS], Nv[NS], A[NS], B[NS];
-            contract<L>(Of, Nf);
+            contract<L>(Om, Nf);
             contract<L>(Ov, Nv);
 #pragma unroll
             for (int c = 0; c < NS; ++c) {
                 A[c] = kS * Nf[c];
                 B[c] = kS * Nv[c];
             }
-            tau = solve_tau<L, R, CLOSURE>(A, B, a, S);
+            tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
             if (a.readout) goto readout;
-            const R snu = R(1) / tau;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) out[i] = fma(snu, Ov[i], Of[i]) - g[i];
+            sfor<Q>([&](auto i) { out[i] = fma(snu, Ov[i], Om[i]); });
+        }
+        if constexpr (FORCE) {  // f* = f - Omega + Fbar
+            out[0] -= F0;
+            sfor<NP>([&](auto p) {
+                out[L::pa(CV(p))] -= R(0.5) * (PF[p] + DF[p]);
+                out[L::pb(CV(p))] -= R(0.5) * (PF[p] - DF[p]);
+            });
         }
     }
 
-    {
-        ST* __restrict__ dst = static_cast<ST*>(a.dst);
-        sfor<Q>([&](auto i) { Store<ST>::st(dst + CV(i) * a.stride + node, f[i] - out[i]); });
-    }
+    sfor<Q>([&](auto i) { Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + node, f[i] - out[i]); });
     return;
 
 readout:
@@ -743,44 +908,58 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
 }
 
 // ------------------------------------------------------------------------------------------
-// global sums in FP64: per-block partials into scratch, then one ordered final pass
+// global sums: each block walks whole rows (fixed assignment, so the result is reproducible);
+// FP32 states accumulate with an error-free two-sum (hi, lo) pair per component, FP64 states in
+// plain FP64; per-block partials go to scratch as FP64 and one ordered pass adds them.
 
 constexpr int SUM_THREADS = 256;
+
+template <class R>
+struct Comp {
+    R hi = R(0), lo = R(0);
+    __device__ __forceinline__ void add(R x) {
+        if constexpr (sizeof(R) == 4) {
+            const R t = hi + x;
+            const R bp = t - hi;
+            lo += (hi - (t - bp)) + (x - bp);
+            hi = t;
+        } else {
+            hi += x;
+        }
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
 
 template <class L, class ST>
 __global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename Store<ST>::R> a, double* __restrict__ partial) {
     using R = typename Store<ST>::R;
     constexpr int D = L::D;
     const int N = a.nx * a.ny * a.nz;
-    double acc[1 + D];
-#pragma unroll
-    for (int c = 0; c <= D; ++c) acc[c] = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-        const int x = n % a.nx;
-        const int y = (n / a.nx) % a.ny;
-        const int z = n / (a.nx * a.ny);
-        R f[L::Q];
-        pull<L, ST, R>(a, x, y, z, f);
-        sfor<L::Q>([&](auto i) {
-            const double v = double(f[i]);
-            acc[0] += v;
-            sfor<D>([&](auto d) {
-                constexpr int cd = L::c(CV(i), CV(d));
-                if constexpr (cd == 1) acc[1 + CV(d)] += v;
-                if constexpr (cd == -1) acc[1 + CV(d)] -= v;
+    const int rows = a.ny * a.nz;
+    Comp<R> acc[1 + D];
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = r % a.ny, z = r / a.ny;
+        for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
+            R f[L::Q];
+            pull<L, ST, R>(a, x, y, z, f);
+            sfor<L::Q>([&](auto i) {
+                acc[0].add(f[i]);
+                sfor<D>([&](auto d) {
+                    constexpr int cd = L::c(CV(i), CV(d));
+                    if constexpr (cd == 1) acc[1 + CV(d)].add(f[i]);
+                    if constexpr (cd == -1) acc[1 + CV(d)].add(-f[i]);
+                });
             });
-        });
+            const int n = r * a.nx + x;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const double Fd = a.force_field ? double(a.force_field[d * N + n]) : double(a.F[d]);
-            acc[1 + d] += 0.5 * Fd;
+            for (int d = 0; d < D; ++d) acc[1 + d].add(R(0.5) * (a.force_field ? a.force_field[d * N + n] : a.F[d]));
         }
     }
     __shared__ double red[SUM_THREADS / 32][1 + D];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c <= D; ++c) {
-        double v = acc[c];
+        double v = acc[c].value();
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][c] = v;
     }

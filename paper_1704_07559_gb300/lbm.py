@@ -128,7 +128,8 @@ class Lattice:
         p.formula = FORMULA[formula]
         p.smag_iters = smag_iters
         p.pl_max_iter = pl_max_iter
-        bc = bc if bc is not None else ["periodic"] * 6
+        bc = list(bc) if bc is not None else ["periodic"] * 6
+        bc += ["periodic"] * (6 - len(bc))  # 2D lattices may give only the four x / y faces
         for f in range(6):
             p.bc[f] = BC[bc[f]] if isinstance(bc[f], str) else int(bc[f])
         p.force_field = 1 if force_field is not None else 0

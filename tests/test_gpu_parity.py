@@ -48,7 +48,8 @@ class Case:
         self.q, self.dims, self.precision = q, dims, precision
         self.d = 3 if q == 19 else 2
         self.shape = (dims[2], dims[1], dims[0])
-        self.bc = bc or ["periodic"] * 6
+        self.bc = list(bc or ["periodic"] * 6)
+        self.bc += ["periodic"] * (6 - len(self.bc))
         self.lid = lid or {}
         rng = np.random.default_rng(seed)
         self.force = force
