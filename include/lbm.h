@@ -164,6 +164,37 @@ int lbm_sums(lbm_ctx* ctx, double* out);
 int lbm_get_state(lbm_ctx* ctx, void* dst);
 int lbm_set_state(lbm_ctx* ctx, const void* src);
 
+/* Allocation-free global sums (the paper has no counterpart: this is a library service).
+ *
+ * Same result as lbm_sums, for callers that cannot allocate device memory at the point where
+ * they need the sums: lbm_create allocates the context's scratch with cudaMalloc, which such
+ * callers must avoid, e.g. code whose device memory belongs to another allocator (a framework's
+ * caching pool) or a time-stepping loop with a latency budget (cudaMalloc / cudaFree may
+ * synchronise the device and take unbounded time).  No context is used and nothing is allocated:
+ * no cudaMalloc, cudaFree or allocating library routine is called.
+ *  lattice, nx, ny, nz  as for lbm_create;  p: precision, bc, lid_u and rho0 are read;
+ *  force    d components of the uniform force density, or NULL;
+ *  f        device pointer to one population buffer (q arrays of `stride` elements of the
+ *           storage type, stride >= nx*ny*nz), holding post-collision populations as after
+ *           lbm_step; the sums are those of the state the next step would see;
+ *  force_field  d x N values of the compute type, or NULL (then `force` applies);
+ *  out      HOST pointer to d+1 doubles: [sum delta rho, sum j_x, sum j_y, (sum j_z)];
+ *  stream   cudaStream_t as void* (NULL = legacy default stream); the call synchronises it.
+ * The scratch is one static device array of LBM_NOALLOC_MAX_BLOCKS x 4 partial sums (plus 4
+ * doubles) that every GPU loading the library holds until the process exits.  Lattices with
+ * more than LBM_NOALLOC_MAX_ROWS rows (ny * nz) are rejected with LBM_ERR_ARG, as are the other
+ * argument errors of lbm_create; a rejected call touches no CUDA state.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Each call writes every scratch slot it reads,
+ * so nothing has to be cleared between calls, but all calls share the one array: calls whose
+ * kernels can overlap on the GPU (other streams or host threads) race and must be serialised.
+ * Returns LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, or LBM_ERR_NONFINITE (out filled) for a NaN or
+ * infinite sum. */
+#define LBM_NOALLOC_MAX_BLOCKS 16384
+#define LBM_NOALLOC_MAX_ROWS (16 * LBM_NOALLOC_MAX_BLOCKS)
+int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_params* p, const double* force,
+                     const void* f, int64_t stride, const void* force_field, double* out, void* stream);
+
 /* Message of the last failed call on ctx (empty if none), owned by the context.  With ctx = NULL:
  * the message of the last failed lbm_create on the calling thread. */
 const char* lbm_last_error(const lbm_ctx* ctx);

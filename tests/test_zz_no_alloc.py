@@ -1,0 +1,86 @@
+"""The allocation-free sums entry point (lbm_sums_noalloc) against the regular lbm_sums.
+
+lbm_sums_noalloc serves callers that cannot allocate device memory when they need the global
+mass and momentum sums (their memory belongs to another allocator, or they run a time-stepping
+loop where cudaMalloc may synchronise the device).  It keeps its scratch in a static device
+array instead of the context's cudaMalloc'ed buffer.  This file is collected last so that a run
+stopping at the first failure has already run every other test; it passes both alone in a fresh
+process and after the others.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1704_07559_gb300 import build, lbm
+
+RATES19 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / 0.51, 1.4, 1 / 0.51, 1.4, 1 / 0.51, 1 / 0.51, 1 / 0.51, 1.98,
+           1.98, 1.98]
+RATES9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / 0.7, 1 / 0.7]
+
+
+def entry():
+    build.build()
+    L = lbm.lib()
+    fn = L.lbm_sums_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lbm.Params),
+                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    return fn
+
+
+def call(fn, lat, buf, force=None):
+    out = (ctypes.c_double * (1 + lat.d))()
+    fv = None if force is None else (ctypes.c_double * 3)(*(list(force) + [0.0] * (3 - len(force))))
+    ff = None if lat.force_field is None else ctypes.c_void_p(lat.force_field.data_ptr())
+    rc = fn(lat.q, lat.nx, lat.ny, lat.nz, ctypes.byref(lat.params), fv, ctypes.c_void_p(buf.data_ptr()), lat.stride,
+            ff, out, ctypes.c_void_p(lat.stream.cuda_stream))
+    return rc, np.array(out[:])
+
+
+def test_rejects_too_many_rows_without_touching_the_gpu():
+    """More than LBM_NOALLOC_MAX_ROWS rows (ny * nz) exceed the static scratch: LBM_ERR_ARG."""
+    fn = entry()
+    p = lbm.default_params()
+    out = (ctypes.c_double * 4)()
+    rc = fn(19, 4, 1024, 257, ctypes.byref(p), None, ctypes.c_void_p(16), 4 * 1024 * 257, None, out, None)
+    assert rc == -1
+    rc = fn(19, 4, 4, 4, None, None, ctypes.c_void_p(16), 64, None, out, None)
+    assert rc == -1
+
+
+CASES = [
+    dict(q=19, dims=(70, 12, 9), precision="fp32", bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+         force=[1e-5, 0.0, 2e-6], tol=1e-6),
+    dict(q=19, dims=(40, 10, 8), precision="fp64", bc=None, force=None, tol=1e-13),
+    dict(q=9, dims=(90, 33, 1), precision="fp32", bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)}, force=None,
+         tol=1e-6),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", CASES, ids=["d3q19-fp32-channel", "d3q19-fp64-periodic", "d2q9-fp32-lid"])
+def test_matches_lbm_sums_on_two_calls_in_a_row(case):
+    """Two calls in a row (before and after a step, so the scratch holds the first call's
+    contents when the second runs) agree with lbm_sums within the sums tolerance of the parity
+    tests (1e-13 x N max|f| in FP64, 1e-6 x N max|f| otherwise)."""
+    import torch
+
+    fn = entry()
+    q = case["q"]
+    rng = np.random.default_rng(11)
+    lat = lbm.Lattice(q, *case["dims"], rates=RATES19 if q == 19 else RATES9, precision=case["precision"],
+                      closure="smag", smag_cs=0.17, bc=case["bc"], lid_u=case.get("lid"), force=case["force"])
+    d = lat.d
+    lat.init(rng.normal(scale=1e-3, size=lat.shape), rng.normal(scale=0.02, size=(d,) + lat.shape),
+             rng.normal(scale=2e-3, size=(d * d,) + lat.shape))
+    bufs = [lat.f_a, lat.f_b]
+    for call_no in range(2):
+        cur = bufs[call_no % 2]  # A after init, B after one step
+        ref = lat.sums()
+        rc, got = call(fn, lat, cur, case["force"])
+        assert rc == 0
+        fmax = float(cur[:, :lat.N].abs().max().to(torch.float64))
+        assert np.abs(got - ref).max() <= case["tol"] * lat.N * fmax, (call_no, got, ref)
+        lat.step(1)
