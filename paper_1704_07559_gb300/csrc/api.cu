@@ -75,7 +75,11 @@ void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
     a->ny = c->ny;
     a->nz = c->nz;
     a->stride = c->stride;
-    for (int k = 0; k < 19; ++k) a->s[k] = R(k < c->q ? c->rates[k] : 0.0);
+    for (int k = 0; k < 19; ++k) {
+        a->s[k] = R(k < c->q ? c->rates[k] : 0.0);
+        const int n2 = k >= c->q ? 1 : (c->q == 19 ? lbm::norm2<lbm::D3Q19>(k) : lbm::norm2<lbm::D2Q9>(k));
+        a->skn[k] = R(k < c->q ? c->rates[k] / n2 : 0.0);
+    }
     for (int d = 0; d < 3; ++d) a->F[d] = R(c->force[d]);
     a->rho0 = R(c->p.rho0);
     a->inv_rho0 = R(1.0 / c->p.rho0);

@@ -1,10 +1,10 @@
 // step.cuh -- the fused MRT lattice Boltzmann step and its read-out, init and sum kernels.
 //
-// One thread owns one lattice node.  A step pulls the node's 19 (or 9) pre-collision
-// populations from the previous post-collision buffer (f_i(x) = f*_i(x - c_i), Sec. 2
-// eq. (mrteq)), forms S by Yu's formula (eq. (LuoS)) or Chai's formula (eq. (ChaiS)), solves the
-// strain-rate closure for tau, relaxes in moment space (eq. (mrteqvT)) with the discrete force,
-// and stores f* at the node: a single pass over HBM, 2 q values per node.
+// A step pulls each node's 19 (or 9) pre-collision populations from the previous post-collision
+// buffer (f_i(x) = f*_i(x - c_i), Sec. 2 eq. (mrteq)), forms S by Yu's formula (eq. (LuoS)) or
+// Chai's formula (eq. (ChaiS)), solves the strain-rate closure for tau, relaxes in moment space
+// (eq. (mrteqvT)) with the discrete force, and stores f* at the node: a single pass over HBM,
+// 2 q values per node.
 //
 // Both routes write the collision in "delta form", f* = f - (increment), so that the
 // storage-precision rounding acts only on the small collision increment:
@@ -16,6 +16,9 @@
 // w_i[(c_i - u).F/cs^2 + (c_i.u)(c_i.F)/cs^4]; it equals the j-derivative of m_eq along F.
 // With a closure the viscous rates are unknown, so both routes split S = A + s_nu B (exact:
 // S is linear in the rates) and solve the scalar fixed point for tau = 1/s_nu.
+//
+// A thread owns VW x-adjacent nodes: VW = 1 (scalar R = float or double), or VW = 2 with R = F2,
+// the packed pair of vec2.cuh, so each arithmetic instruction advances both nodes.
 //
 // All lattice coefficients enter as compile-time constants: loops over populations and moments
 // are compile-time sequences (sfor) so each entry of T and c folds into an add, a subtract or
@@ -31,6 +34,7 @@
 #include <utility>
 
 #include "lattice.cuh"
+#include "vec2.cuh"
 
 namespace lbm {
 
@@ -60,15 +64,23 @@ __device__ __forceinline__ R cadd(R acc, R x) {
     else if constexpr (T == -1)
         return acc - x;
     else
-        return acc + R(T) * x;
+        return fma(R(float(T)), x, acc);
 }
 template <class R>
 __device__ __forceinline__ constexpr R nzero() {
-    return R(-0.0);
+    return R(-0.0f);
+}
+// a constant given in double, rounded once to the compute type (exact for the FP64 path)
+template <class R>
+__device__ __forceinline__ constexpr R cst(double c) {
+    if constexpr (std::is_same<R, double>::value)
+        return c;
+    else
+        return R(float(c));
 }
 
 // ------------------------------------------------------------------------------------------
-// storage types
+// storage types: scalar access, and the pair access of the two-node path
 
 template <class ST>
 struct Store;
@@ -83,24 +95,35 @@ struct Store<float> {
     using R = float;
     static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, R v) { __stcs(p, v); }
+    // aligned pair p[0], p[1] (p 8-byte aligned)
+    static __device__ __forceinline__ F2 ld2(const float* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
+    static __device__ __forceinline__ void st2(float* p, F2 v) { __stcs(reinterpret_cast<float2*>(p), v.v); }
 };
 template <>
 struct Store<__half> {
     using R = float;
     static __device__ __forceinline__ R ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ F2 ld2(const __half* p) {
+        return F2(__half22float2(__ldg(reinterpret_cast<const __half2*>(p))));
+    }
+    static __device__ __forceinline__ void st2(__half* p, F2 v) {
+        *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
+    }
 };
 template <>
 struct Store<__nv_bfloat16> {
     using R = float;
     static __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ F2 ld2(const __nv_bfloat16* p) {
+        return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p))));
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16* p, F2 v) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+    }
 };
 
-__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float r_pow(float x, float y) { return powf(x, y); }
-__device__ __forceinline__ double r_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float r_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double r_abs(double x) { return fabs(x); }
 // Closure arithmetic: in FP32 the fast reciprocal / reciprocal-square-root / power intrinsics
@@ -113,31 +136,32 @@ __device__ __forceinline__ float c_pow(float x, float y) { return y == 0.0f ? 1.
 __device__ __forceinline__ double c_pow(double x, double y) { return pow(x, y); }
 
 // ------------------------------------------------------------------------------------------
-// kernel arguments (by value)
+// kernel arguments (by value; scalar type RS = float or double)
 
-template <class R>
+template <class RS>
 struct StepArgs {
     int nx, ny, nz;
-    int readout;          // 0: step (write f*); 1: write S/tau/drho/u of the pre-collision state
-    long long stride;     // elements between population arrays
-    const void* src;      // post-collision buffer of the previous step
-    void* dst;            // post-collision buffer of this step
-    const void* srcp[19]; // src + i * stride, population i (filled on the host)
-    void* dstp[19];       // dst + i * stride
-    const R* force_field; // d x N, or nullptr for the uniform force F
-    R F[3];
-    R s[19];              // relaxation rates; the viscous entries hold 1/tau0
-    R rho0, inv_rho0, tau0;
-    R smag_c3;            // 3 Cs^2
-    R pl_k3, pl_nm1, pl_tau_min, pl_tau_max, pl_tol;  // 3K, n-1, clamp, tolerance
+    int readout;           // 0: step (write f*); 1: write S/tau/drho/u of the pre-collision state
+    long long stride;      // elements between population arrays
+    const void* src;       // post-collision buffer of the previous step
+    void* dst;             // post-collision buffer of this step
+    const void* srcp[19];  // src + i * stride, population i (filled on the host)
+    void* dstp[19];        // dst + i * stride
+    const RS* force_field; // d x N, or nullptr for the uniform force F
+    RS F[3];
+    RS s[19];              // relaxation rates; the viscous entries hold 1/tau0
+    RS skn[19];            // s_k / |T_k|^2
+    RS rho0, inv_rho0, tau0;
+    RS smag_c3;            // 3 Cs^2
+    RS pl_k3, pl_nm1, pl_tau_min, pl_tau_max, pl_tol;  // 3K, n-1, clamp, tolerance
     int smag_iters, pl_max_iter;
-    int wall_mask;        // bit f: face f is not periodic (wall or lid)
-    int lid_mask;         // bit f: face f is a moving wall
-    R lid[6][3];
-    R* S_out;
-    R* tau_out;
-    R* drho_out;
-    R* u_out;
+    int wall_mask;         // bit f: face f is not periodic (wall or lid)
+    int lid_mask;          // bit f: face f is a moving wall
+    RS lid[6][3];
+    RS* S_out;
+    RS* tau_out;
+    RS* drho_out;
+    RS* u_out;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -253,17 +277,17 @@ struct Xf<D3Q19> {
         m[3] = D[0] + Ex;
         m[5] = D[1] + Ey;
         m[7] = D[2] + Ez;
-        m[4] = fma(R(-4), D[0], Ex);
-        m[6] = fma(R(-4), D[1], Ey);
-        m[8] = fma(R(-4), D[2], Ez);
-        m[1] = fma(R(8), Sed, fma(R(-11), Sax, R(-30) * f0));
-        m[2] = fma(R(-4), Sax, fma(R(12), f0, Sed));
-        const R Qm = fma(R(-2), Eyz, Q);
-        m[9] = fma(R(2), P[0], Qm - Pyz);
-        m[10] = fma(R(-4), P[0], fma(R(2), Pyz, Qm));
+        m[4] = fma(R(-4.0f), D[0], Ex);
+        m[6] = fma(R(-4.0f), D[1], Ey);
+        m[8] = fma(R(-4.0f), D[2], Ez);
+        m[1] = fma(R(8.0f), Sed, fma(R(-11.0f), Sax, R(-30.0f) * f0));
+        m[2] = fma(R(-4.0f), Sax, fma(R(12.0f), f0, Sed));
+        const R Qm = fma(R(-2.0f), Eyz, Q);
+        m[9] = fma(R(2.0f), P[0], Qm - Pyz);
+        m[10] = fma(R(-4.0f), P[0], fma(R(2.0f), Pyz, Qm));
         const R dyz = P[1] - P[2], dxyz = Exy - Exz;
         m[11] = dyz + dxyz;
-        m[12] = fma(R(-2), dyz, dxyz);
+        m[12] = fma(R(-2.0f), dyz, dxyz);
         m[13] = P[3] - P[4];
         m[14] = P[7] - P[8];
         m[15] = P[5] - P[6];
@@ -282,19 +306,24 @@ struct Xf<D3Q19> {
             back_transform<D3Q19, USE>(a, out);
         } else {
             constexpr bool CONS = (USE >> 3) & 1u;
-            out[0] = fma(R(12), a[2], R(-30) * a[1]);
+            out[0] = fma(R(12.0f), a[2], R(-30.0f) * a[1]);
             // axis populations
-            const R B1 = fma(R(-4), a[2], R(-11) * a[1]);
-            const R C = fma(R(2), a[10], -a[9]);
-            const R W = fma(R(-2), a[12], a[11]);
-            const R Ex = fma(R(-2), C, B1);
-            const R Ey = B1 + C + W;
-            const R Ez = B1 + C - W;
-            R Ox = R(-4) * a[4], Oy = R(-4) * a[6], Oz = R(-4) * a[8];
+            const R B1 = fma(R(-4.0f), a[2], R(-11.0f) * a[1]);
+            const R C = fma(R(2.0f), a[10], -a[9]);
+            const R W = fma(R(-2.0f), a[12], a[11]);
+            const R Ex = fma(R(-2.0f), C, B1);
+            const R BC = B1 + C;
+            const R Ey = BC + W;
+            const R Ez = BC - W;
+            R Ox, Oy, Oz;
             if constexpr (CONS) {
-                Ox += a[3];
-                Oy += a[5];
-                Oz += a[7];
+                Ox = fma(R(-4.0f), a[4], a[3]);
+                Oy = fma(R(-4.0f), a[6], a[5]);
+                Oz = fma(R(-4.0f), a[8], a[7]);
+            } else {
+                Ox = R(-4.0f) * a[4];
+                Oy = R(-4.0f) * a[6];
+                Oz = R(-4.0f) * a[8];
             }
             out[1] = Ex + Ox;
             out[2] = Ex - Ox;
@@ -303,7 +332,7 @@ struct Xf<D3Q19> {
             out[5] = Ez + Oz;
             out[6] = Ez - Oz;
             // edge populations
-            const R B2 = fma(R(8), a[1], a[2]);
+            const R B2 = fma(R(8.0f), a[1], a[2]);
             const R G = a[9] + a[10], H = a[11] + a[12];
             R X = a[4], Y = a[6], Z = a[8];
             if constexpr (CONS) {
@@ -311,8 +340,9 @@ struct Xf<D3Q19> {
                 Y += a[5];
                 Z += a[7];
             }
+            const R BG = B2 + G;
             {  // xy edges: (7,10) and (8,9)
-                const R base = B2 + G + H;
+                const R base = BG + H;
                 const R E4 = base + a[13], E5 = base - a[13];
                 const R u = X + a[16], v = Y - a[17];
                 const R O4 = v + u, O5 = v - u;
@@ -322,7 +352,7 @@ struct Xf<D3Q19> {
                 out[9] = E5 - O5;
             }
             {  // xz edges: (11,14) and (12,13)
-                const R base = B2 + G - H;
+                const R base = BG - H;
                 const R E6 = base + a[15], E7 = base - a[15];
                 const R u = X - a[16], v = Z + a[18];
                 const R O6 = v + u, O7 = v - u;
@@ -332,7 +362,7 @@ struct Xf<D3Q19> {
                 out[13] = E7 - O7;
             }
             {  // yz edges: (15,18) and (16,17)
-                const R base = fma(R(-2), G, B2);
+                const R base = fma(R(-2.0f), G, B2);
                 const R E8 = base + a[14], E9 = base - a[14];
                 const R u = Y + a[17], v = Z - a[18];
                 const R O8 = v + u, O9 = v - u;
@@ -357,7 +387,8 @@ __device__ __forceinline__ void contract(const R (&v)[L::Q], R (&N)[L::NS]) {
 }
 
 // ------------------------------------------------------------------------------------------
-// equilibrium moments (closed form) and force moments TF = d m_eq / d j . F
+// equilibrium moments (closed form) and force moments TF = d m_eq / d j . F, both written with
+// u = j / rho0 formed once
 
 template <class L>
 struct Eq;
@@ -366,148 +397,154 @@ template <>
 struct Eq<D3Q19> {
     // eq. (meq): w_eps = 3, w_epsj = -11/2, w_xx = -1/2
     template <class R>
-    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], R ir0, R (&m)[19]) {
-        const R jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
+    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], const R (&u)[3], R (&m)[19]) {
+        const R ju = fma(j[0], u[0], fma(j[1], u[1], j[2] * u[2]));
         m[0] = drho;
-        m[1] = R(-11) * drho + R(19) * jj;
-        m[2] = R(3) * drho - R(5.5) * jj;
+        m[1] = fma(R(19.0f), ju, R(-11.0f) * drho);
+        m[2] = fma(R(-5.5f), ju, R(3.0f) * drho);
         m[3] = j[0];
-        m[4] = R(-2.0 / 3.0) * j[0];
+        m[4] = cst<R>(-2.0 / 3.0) * j[0];
         m[5] = j[1];
-        m[6] = R(-2.0 / 3.0) * j[1];
+        m[6] = cst<R>(-2.0 / 3.0) * j[1];
         m[7] = j[2];
-        m[8] = R(-2.0 / 3.0) * j[2];
-        m[9] = R(3) * j[0] * j[0] * ir0 - jj;
-        m[10] = R(-0.5) * m[9];
-        m[11] = (j[1] * j[1] - j[2] * j[2]) * ir0;
-        m[12] = R(-0.5) * m[11];
-        m[13] = j[0] * j[1] * ir0;
-        m[14] = j[1] * j[2] * ir0;
-        m[15] = j[0] * j[2] * ir0;
-        m[16] = R(0);
-        m[17] = R(0);
-        m[18] = R(0);
+        m[8] = cst<R>(-2.0 / 3.0) * j[2];
+        m[9] = fma(R(3.0f) * j[0], u[0], -ju);
+        m[10] = R(-0.5f) * m[9];
+        m[11] = fma(j[1], u[1], -(j[2] * u[2]));
+        m[12] = R(-0.5f) * m[11];
+        m[13] = j[0] * u[1];
+        m[14] = j[1] * u[2];
+        m[15] = j[0] * u[2];
+        m[16] = R(0.0f);
+        m[17] = R(0.0f);
+        m[18] = R(0.0f);
     }
     template <class R>
-    static __device__ __forceinline__ void tforce(const R (&j)[3], const R (&F)[3], R ir0, R (&t)[19]) {
-        const R jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
-        t[0] = R(0);
-        t[1] = R(38) * jF;
-        t[2] = R(-11) * jF;
+    static __device__ __forceinline__ void tforce(const R (&u)[3], const R (&F)[3], R (&t)[19]) {
+        const R uF = fma(u[0], F[0], fma(u[1], F[1], u[2] * F[2]));
+        t[0] = R(0.0f);
+        t[1] = R(38.0f) * uF;
+        t[2] = R(-11.0f) * uF;
         t[3] = F[0];
-        t[4] = R(-2.0 / 3.0) * F[0];
+        t[4] = cst<R>(-2.0 / 3.0) * F[0];
         t[5] = F[1];
-        t[6] = R(-2.0 / 3.0) * F[1];
+        t[6] = cst<R>(-2.0 / 3.0) * F[1];
         t[7] = F[2];
-        t[8] = R(-2.0 / 3.0) * F[2];
-        t[9] = R(6) * j[0] * F[0] * ir0 - R(2) * jF;
-        t[10] = R(-0.5) * t[9];
-        t[11] = R(2) * (j[1] * F[1] - j[2] * F[2]) * ir0;
-        t[12] = R(-0.5) * t[11];
-        t[13] = (j[0] * F[1] + j[1] * F[0]) * ir0;
-        t[14] = (j[1] * F[2] + j[2] * F[1]) * ir0;
-        t[15] = (j[0] * F[2] + j[2] * F[0]) * ir0;
-        t[16] = R(0);
-        t[17] = R(0);
-        t[18] = R(0);
+        t[8] = cst<R>(-2.0 / 3.0) * F[2];
+        t[9] = fma(R(6.0f) * u[0], F[0], R(-2.0f) * uF);
+        t[10] = R(-0.5f) * t[9];
+        t[11] = R(2.0f) * fma(u[1], F[1], -(u[2] * F[2]));
+        t[12] = R(-0.5f) * t[11];
+        t[13] = fma(u[0], F[1], u[1] * F[0]);
+        t[14] = fma(u[1], F[2], u[2] * F[1]);
+        t[15] = fma(u[0], F[2], u[2] * F[0]);
+        t[16] = R(0.0f);
+        t[17] = R(0.0f);
+        t[18] = R(0.0f);
     }
     // moments with identically zero equilibrium and force parts (ghost moments t_x, t_y, t_z)
     static __host__ __device__ constexpr bool ghost(int k) { return k >= 16; }
-    // Yu formula eq. (LuoS) split as S = A + s_nu B (A: the s1 m1 part)
+    // Yu formula eq. (LuoS) split as S = A + s_nu B (A: the s1 m1 part); c1 = s1/(38 rho0), ir0 = 1/rho0
     template <class R>
-    static __device__ __forceinline__ void yu_split(const R (&mn)[19], R s1, R ir0, R (&A)[6], R (&B)[6]) {
-        const R a = -s1 * mn[1] * (R(1.0 / 38.0) * ir0);
+    static __device__ __forceinline__ void yu_split(const R (&mn)[19], R c1, R ir0, R (&A)[6], R (&B)[6]) {
+        const R a = -(c1 * mn[1]);
         A[0] = a;
         A[1] = a;
         A[2] = a;
-        A[3] = R(0);
-        A[4] = R(0);
-        A[5] = R(0);
-        B[0] = R(-0.5) * ir0 * mn[9];
-        B[1] = R(0.25) * ir0 * fma(R(-3), mn[11], mn[9]);
-        B[2] = R(0.25) * ir0 * fma(R(3), mn[11], mn[9]);
-        B[3] = R(-1.5) * ir0 * mn[13];
-        B[4] = R(-1.5) * ir0 * mn[14];
-        B[5] = R(-1.5) * ir0 * mn[15];
+        A[3] = R(0.0f);
+        A[4] = R(0.0f);
+        A[5] = R(0.0f);
+        const R h = R(0.25f) * ir0;
+        const R k = R(-1.5f) * ir0;
+        B[0] = (R(-0.5f) * ir0) * mn[9];
+        B[1] = h * fma(R(-3.0f), mn[11], mn[9]);
+        B[2] = h * fma(R(3.0f), mn[11], mn[9]);
+        B[3] = k * mn[13];
+        B[4] = k * mn[14];
+        B[5] = k * mn[15];
     }
+    static constexpr double YU_A = 1.0 / 38.0;  // c1 = s1 * YU_A / rho0
 };
 
 template <>
 struct Eq<D2Q9> {
     template <class R>
-    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], R ir0, R (&m)[9]) {
-        const R jj = (j[0] * j[0] + j[1] * j[1]) * ir0;
+    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], const R (&u)[3], R (&m)[9]) {
+        const R ju = fma(j[0], u[0], j[1] * u[1]);
         m[0] = drho;
-        m[1] = R(-2) * drho + R(3) * jj;
-        m[2] = drho - R(3) * jj;
+        m[1] = fma(R(3.0f), ju, R(-2.0f) * drho);
+        m[2] = fma(R(-3.0f), ju, drho);
         m[3] = j[0];
         m[4] = -j[0];
         m[5] = j[1];
         m[6] = -j[1];
-        m[7] = (j[0] * j[0] - j[1] * j[1]) * ir0;
-        m[8] = j[0] * j[1] * ir0;
+        m[7] = fma(j[0], u[0], -(j[1] * u[1]));
+        m[8] = j[0] * u[1];
     }
     template <class R>
-    static __device__ __forceinline__ void tforce(const R (&j)[3], const R (&F)[3], R ir0, R (&t)[9]) {
-        const R jF = (j[0] * F[0] + j[1] * F[1]) * ir0;
-        t[0] = R(0);
-        t[1] = R(6) * jF;
-        t[2] = R(-6) * jF;
+    static __device__ __forceinline__ void tforce(const R (&u)[3], const R (&F)[3], R (&t)[9]) {
+        const R uF = fma(u[0], F[0], u[1] * F[1]);
+        t[0] = R(0.0f);
+        t[1] = R(6.0f) * uF;
+        t[2] = R(-6.0f) * uF;
         t[3] = F[0];
         t[4] = -F[0];
         t[5] = F[1];
         t[6] = -F[1];
-        t[7] = R(2) * (j[0] * F[0] - j[1] * F[1]) * ir0;
-        t[8] = (j[0] * F[1] + j[1] * F[0]) * ir0;
+        t[7] = R(2.0f) * fma(u[0], F[0], -(u[1] * F[1]));
+        t[8] = fma(u[0], F[1], u[1] * F[0]);
     }
     static __host__ __device__ constexpr bool ghost(int) { return false; }
     // Yu-type D2Q9 formula (Sec. 5.4 procedure): S_xx,yy = -(s_e m_e +- 3 s_nu m_pxx)/(4 rho0),
-    // S_xy = -3 s_nu m_pxy / (2 rho0)
+    // S_xy = -3 s_nu m_pxy / (2 rho0);  c1 = s_e/(4 rho0)
     template <class R>
-    static __device__ __forceinline__ void yu_split(const R (&mn)[9], R se, R ir0, R (&A)[3], R (&B)[3]) {
-        const R a = -se * mn[1] * (R(0.25) * ir0);
+    static __device__ __forceinline__ void yu_split(const R (&mn)[9], R c1, R ir0, R (&A)[3], R (&B)[3]) {
+        const R a = -(c1 * mn[1]);
         A[0] = a;
         A[1] = a;
-        A[2] = R(0);
-        B[0] = R(-0.75) * ir0 * mn[7];
-        B[1] = R(0.75) * ir0 * mn[7];
-        B[2] = R(-1.5) * ir0 * mn[8];
+        A[2] = R(0.0f);
+        const R h = R(0.75f) * ir0;
+        B[0] = -(h * mn[7]);
+        B[1] = h * mn[7];
+        B[2] = (R(-1.5f) * ir0) * mn[8];
     }
+    static constexpr double YU_A = 1.0 / 4.0;
 };
 
 // He-Luo equilibrium (eq. (edf), delta-rho form) and the discrete force in opposite-pair form:
-// Pe_p = feq_a + feq_b = 2 w (drho + 4.5 (c.j)^2/rho0 - 1.5 j.j/rho0), De_p = feq_a - feq_b =
-// 6 w c.j;  PF_p = Fbar_a + Fbar_b = 2 w (9 (c.j)(c.F) - 3 j.F)/rho0, DF_p = 6 w c.F;
-// rest: fe0 = w0 (drho - 1.5 j.j/rho0), F0 = -3 w0 j.F/rho0.  (c = c_a, w = w_a.)
+// Pe_p = feq_a + feq_b = 2 w (drho + 4.5 (c.j)(c.u) - 1.5 j.u), De_p = feq_a - feq_b = 6 w c.j;
+// PF_p = Fbar_a + Fbar_b = 2 w (9 (c.u)(c.F) - 3 u.F), DF_p = 6 w c.F;
+// rest: fe0 = w0 (drho - 1.5 j.u), F0 = -3 w0 u.F.  (c = c_a, w = w_a, u = j / rho0.)
 template <class L, bool FORCE, class R>
-__device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const R (&F)[3], R ir0, R& fe0,
+__device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const R (&u)[3], const R (&F)[3], R& fe0,
                                                   R (&Pe)[L::NP], R (&De)[L::NP], R& F0, R (&PF)[L::NP],
                                                   R (&DF)[L::NP]) {
-    const R jj = (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) * ir0;
-    const R base = fma(R(-1.5), jj, drho);
-    constexpr R w0 = R(L::w36(0) / 36.0);
-    fe0 = w0 * base;
-    R jF = R(0);
+    const R ju = fma(j[0], u[0], fma(j[1], u[1], j[2] * u[2]));
+    const R base = fma(R(-1.5f), ju, drho);
+    constexpr double w0 = L::w36(0) / 36.0;
+    fe0 = cst<R>(w0) * base;
+    R uF = R(0.0f);
     if constexpr (FORCE) {
-        jF = (j[0] * F[0] + j[1] * F[1] + j[2] * F[2]) * ir0;
-        F0 = R(-3) * w0 * jF;
+        uF = fma(u[0], F[0], fma(u[1], F[1], u[2] * F[2]));
+        F0 = cst<R>(-3.0 * w0) * uF;
     } else {
-        F0 = R(0);
+        F0 = R(0.0f);
     }
     sfor<L::NP>([&](auto p) {
         constexpr int i = L::pa(CV(p));
         constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-        constexpr R w = R(L::w36(i) / 36.0);
+        constexpr double w = L::w36(i) / 36.0;
         const R cj = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), j[0]), j[1]), j[2]);
-        Pe[p] = (R(2) * w) * fma(R(4.5) * cj, cj * ir0, base);
-        De[p] = (R(6) * w) * cj;
+        const R cu = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), u[0]), u[1]), u[2]);
+        Pe[p] = cst<R>(2.0 * w) * fma(R(4.5f) * cj, cu, base);
+        De[p] = cst<R>(6.0 * w) * cj;
         if constexpr (FORCE) {
             const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
-            PF[p] = (R(2) * w) * fma(R(9) * cj, cF * ir0, R(-3) * jF);
-            DF[p] = (R(6) * w) * cF;
+            PF[p] = cst<R>(2.0 * w) * fma(R(9.0f) * cu, cF, R(-3.0f) * uF);
+            DF[p] = cst<R>(6.0 * w) * cF;
         } else {
-            PF[p] = R(0);
-            DF[p] = R(0);
+            PF[p] = R(0.0f);
+            DF[p] = R(0.0f);
         }
     });
 }
@@ -520,9 +557,9 @@ __device__ __forceinline__ R strain_dot(const R (&S)[L::NS], const R (&T)[L::NS]
     // S:T with the off-diagonal components counted twice
     if constexpr (L::NS == 6)
         return fma(S[0], T[0], fma(S[1], T[1], S[2] * T[2])) +
-               R(2) * fma(S[3], T[3], fma(S[4], T[4], S[5] * T[5]));
+               R(2.0f) * fma(S[3], T[3], fma(S[4], T[4], S[5] * T[5]));
     else
-        return fma(S[0], T[0], S[1] * T[1]) + R(2) * S[2] * T[2];
+        return fma(S[0], T[0], S[1] * T[1]) + R(2.0f) * (S[2] * T[2]);
 }
 
 template <class L, class R>
@@ -531,39 +568,55 @@ __device__ __forceinline__ void affine(const R (&A)[L::NS], const R (&B)[L::NS],
     for (int c = 0; c < L::NS; ++c) S[c] = fma(s, B[c], A[c]);
 }
 
-// Returns tau and leaves S = A + B/tau.  |S|^2 = 2 S:S = 2 (a + 2 b s + c s^2) with a = A:A,
-// b = A:B, c = B:B is the exact quadratic in s = 1/tau, so each fixed-point sweep costs a
-// reciprocal, two FMAs and a square root.  Smagorinsky: `smag_iters` sweeps from tau0, stopping
-// early only when a sweep returns its input bit for bit (every later sweep would too).  Power
-// law: sweeps until |tau_new - tau| <= pl_tol tau_new or pl_max_iter sweeps.
-template <class L, class R, int CLOSURE>
-__device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS], const StepArgs<R>& a,
+// Fixed point for tau at one node from the quadratic |S|^2 = 2 (qa + qb2 s + qc s^2), s = 1/tau
+// (qa = A:A, qb2 = 2 A:B, qc = B:B: exact since S = A + s B).  Smagorinsky: `smag_iters` sweeps
+// from tau0, stopping early only when a sweep returns its input bit for bit (every later sweep
+// would too).  Power law: sweeps until |tau_new - tau| <= pl_tol tau_new or pl_max_iter sweeps.
+template <int CLOSURE, class RS>
+__device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepArgs<RS>& a) {
+    RS tau = a.tau0;
+    if constexpr (CLOSURE == CL_SMAG) {
+        for (int it = 0; it < a.smag_iters; ++it) {
+            const RS s = c_rcp(tau);
+            const RS tn = fma(a.smag_c3, c_sqrt(RS(2) * fma(fma(qc, s, qb2), s, qa)), a.tau0);
+            if (tn == tau) break;
+            tau = tn;
+        }
+    } else {
+        for (int it = 1; it <= a.pl_max_iter; ++it) {
+            const RS s = c_rcp(tau);
+            RS tn = fma(a.pl_k3, c_pow(c_sqrt(RS(2) * fma(fma(qc, s, qb2), s, qa)), a.pl_nm1), RS(0.5));
+            if (!(tn >= a.pl_tau_min)) tn = a.pl_tau_min;
+            if (tn > a.pl_tau_max) tn = a.pl_tau_max;
+            const RS diff = r_abs(tn - tau);
+            tau = tn;
+            if (diff <= a.pl_tol * tn) break;
+        }
+    }
+    return tau;
+}
+
+// Returns tau, sets snu = 1/tau and S = A + snu B.  For the packed pair each node solves its own
+// fixed point.
+template <class L, class R, int CLOSURE, class RS>
+__device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS], const StepArgs<RS>& a,
                                        R (&S)[L::NS], R& snu) {
     if constexpr (CLOSURE == CL_NEWTON) {
-        snu = a.s[L::NU0];
+        snu = R(a.s[L::NU0]);
         affine<L>(A, B, snu, S);
-        return a.tau0;
+        return R(a.tau0);
     } else {
-        const R qa = strain_dot<L>(A, A), qb2 = R(2) * strain_dot<L>(A, B), qc = strain_dot<L>(B, B);
-        auto gnorm = [&](R s) { return c_sqrt(R(2) * fma(fma(qc, s, qb2), s, qa)); };
-        R tau = a.tau0;
-        if constexpr (CLOSURE == CL_SMAG) {
-            for (int it = 0; it < a.smag_iters; ++it) {
-                const R tn = fma(a.smag_c3, gnorm(c_rcp(tau)), a.tau0);
-                if (tn == tau) break;
-                tau = tn;
-            }
+        const R qa = strain_dot<L>(A, A), qb2 = R(2.0f) * strain_dot<L>(A, B), qc = strain_dot<L>(B, B);
+        R tau;
+        if constexpr (std::is_same<R, F2>::value) {
+            const float t0 = tau_fixed_point<CLOSURE>(qa.lo(), qb2.lo(), qc.lo(), a);
+            const float t1 = tau_fixed_point<CLOSURE>(qa.hi(), qb2.hi(), qc.hi(), a);
+            tau = F2(t0, t1);
+            snu = F2(c_rcp(t0), c_rcp(t1));
         } else {
-            for (int it = 1; it <= a.pl_max_iter; ++it) {
-                R tn = fma(a.pl_k3, c_pow(gnorm(c_rcp(tau)), a.pl_nm1), R(0.5));
-                if (!(tn >= a.pl_tau_min)) tn = a.pl_tau_min;
-                if (tn > a.pl_tau_max) tn = a.pl_tau_max;
-                const R diff = r_abs(tn - tau);
-                tau = tn;
-                if (diff <= a.pl_tol * tn) break;
-            }
+            tau = tau_fixed_point<CLOSURE>(qa, qb2, qc, a);
+            snu = c_rcp(tau);
         }
-        snu = c_rcp(tau);
         affine<L>(A, B, snu, S);
         return tau;
     }
@@ -578,24 +631,18 @@ __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS],
 // periodic faces wrap, a population whose source lies behind a wall is reflected from the
 // opposite population of the same node, plus the moving-wall term when it crosses exactly one
 // moving face.
-template <class L, class ST, class R>
-__device__ __forceinline__ void pull(const StepArgs<R>& a, int x, int y, int z, R (&f)[L::Q]) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int nxy = nx * ny;
-    const int node = z * nxy + y * nx + x;
+template <class L, class ST, class RS>
+__device__ __forceinline__ bool interior_rows(const StepArgs<RS>& a, int xlo, int xhi, int y, int z) {
     const bool xwall = (a.wall_mask & 3) != 0;
-    bool fast = y > 0 && y < ny - 1 && (!xwall || (x > 0 && x < nx - 1));
-    if constexpr (L::D == 3) fast = fast && z > 0 && z < nz - 1;
-    if (fast) {
-        const int dxm = x == 0 ? nx - 1 : -1;       // source of c_x = +1: x - 1 (wrapped)
-        const int dxp = x == nx - 1 ? 1 - nx : 1;   // source of c_x = -1: x + 1 (wrapped)
-        sfor<L::Q>([&](auto i) {
-            constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
-            const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) - (cy * nx + cz * nxy);
-            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
-        });
-        return;
-    }
+    bool fast = y > 0 && y < a.ny - 1 && (!xwall || (xlo > 0 && xhi < a.nx - 1));
+    if constexpr (L::D == 3) fast = fast && z > 0 && z < a.nz - 1;
+    return fast;
+}
+
+template <class L, class ST, class RS>
+__device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int node = (z * ny + y) * nx + x;
     const int dims[3] = {nx, ny, nz};
     const int pos[3] = {x, y, z};
     sfor<L::Q>([&](auto i) {
@@ -619,25 +666,85 @@ __device__ __forceinline__ void pull(const StepArgs<R>& a, int x, int y, int z, 
         if (nout == 0) {
             f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + (s[2] * ny + s[1]) * nx + s[0]);
         } else {
-            R v = Store<ST>::ld(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + node);
+            RS v = Store<ST>::ld(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + node);
             if (nout == 1 && ((a.lid_mask >> face) & 1)) {
-                const R cu = R(L::c(CV(i), 0)) * a.lid[face][0] + R(L::c(CV(i), 1)) * a.lid[face][1] +
-                             R(L::c(CV(i), 2)) * a.lid[face][2];
-                v += R(L::w36(CV(i)) / 6.0) * a.rho0 * cu;  // 2 w_i rho0 (c.u)/cs^2 = 6 w_i rho0 c.u
+                const RS cu = RS(L::c(CV(i), 0)) * a.lid[face][0] + RS(L::c(CV(i), 1)) * a.lid[face][1] +
+                              RS(L::c(CV(i), 2)) * a.lid[face][2];
+                v += RS(L::w36(CV(i)) / 6.0) * a.rho0 * cu;  // 2 w_i rho0 (c.u)/cs^2 = 6 w_i rho0 c.u
             }
             f[i] = v;
         }
     });
 }
 
+template <class L, class ST, class RS>
+__device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
+    const int nx = a.nx, nxy = a.nx * a.ny;
+    const int node = z * nxy + y * nx + x;
+    if (interior_rows<L, ST>(a, x, x, y, z)) {
+        const int dxm = x == 0 ? nx - 1 : -1;      // source of c_x = +1: x - 1 (wrapped)
+        const int dxp = x == nx - 1 ? 1 - nx : 1;  // source of c_x = -1: x + 1 (wrapped)
+        sfor<L::Q>([&](auto i) {
+            constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+            const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) - (cy * nx + cz * nxy);
+            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
+        });
+        return;
+    }
+    pull_general<L, ST>(a, x, y, z, f);
+}
+
+// Two nodes (x0, x0 + 1), x0 even, nx even: populations with c_x = 0 come as one aligned pair,
+// the others as two scalar loads (x wrap applied per node).
+template <class L, class ST>
+__device__ __forceinline__ void pull2(const StepArgs<float>& a, int x0, int y, int z, F2 (&f)[L::Q]) {
+    const int nx = a.nx, nxy = a.nx * a.ny;
+    const int node = z * nxy + y * nx + x0;
+    if (interior_rows<L, ST>(a, x0, x0 + 1, y, z)) {
+        const int dxm = x0 == 0 ? nx - 1 : -1;          // node 0, c_x = +1: x0 - 1 (wrapped)
+        const int dxp = x0 + 2 == nx ? 2 - nx : 2;      // node 1, c_x = -1: x0 + 2 (wrapped)
+        sfor<L::Q>([&](auto i) {
+            constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+            const ST* p = static_cast<const ST*>(a.srcp[CV(i)]) + (node - (cy * nx + cz * nxy));
+            if constexpr (cx == 0)
+                f[i] = Store<ST>::ld2(p);
+            else if constexpr (cx > 0)
+                f[i] = F2(Store<ST>::ld(p + dxm), Store<ST>::ld(p));
+            else
+                f[i] = F2(Store<ST>::ld(p + 1), Store<ST>::ld(p + dxp));
+        });
+        return;
+    }
+    float f0[L::Q], f1[L::Q];
+    pull_general<L, ST>(a, x0, y, z, f0);
+    pull_general<L, ST>(a, x0 + 1, y, z, f1);
+    sfor<L::Q>([&](auto i) { f[i] = F2(f0[i], f1[i]); });
+}
+
 // ------------------------------------------------------------------------------------------
 // the fused step
 
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+template <class R, class RS>
+__device__ __forceinline__ R load_field(const RS* p) {
+    if constexpr (std::is_same<R, F2>::value)
+        return F2(*reinterpret_cast<const float2*>(p));
+    else
+        return *p;
+}
+template <class R, class RS>
+__device__ __forceinline__ void store_field(RS* p, R v) {
+    if constexpr (std::is_same<R, F2>::value)
+        *reinterpret_cast<float2*>(p) = v.v;
+    else
+        *p = v;
+}
+
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
-    using R = typename Store<ST>::R;
+    using RS = typename Store<ST>::R;
+    using R = std::conditional_t<VW == 2, F2, RS>;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
@@ -645,23 +752,26 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
     const int node = (z * a.ny + y) * a.nx + x;
 
     R f[Q];
-    pull<L, ST, R>(a, x, y, z, f);
+    if constexpr (VW == 2)
+        pull2<L, ST>(a, x, y, z, f);
+    else
+        pull<L, ST>(a, x, y, z, f);
 
     R P[NP], Dd[NP];
     sfor<NP>([&](auto p) {
         P[p] = f[L::pa(CV(p))] + f[L::pb(CV(p))];
         Dd[p] = f[L::pa(CV(p))] - f[L::pb(CV(p))];
     });
-    R F[3] = {R(0), R(0), R(0)};
+    R F[3] = {R(0.0f), R(0.0f), R(0.0f)};
     if constexpr (FORCE) {
         if (a.force_field) {
-            sfor<L::D>([&](auto d) { F[d] = a.force_field[CV(d) * N + node]; });
+            sfor<L::D>([&](auto d) { F[d] = load_field<R>(a.force_field + CV(d) * N + node); });
         } else {
-            sfor<L::D>([&](auto d) { F[d] = a.F[d]; });
+            sfor<L::D>([&](auto d) { F[d] = R(a.F[d]); });
         }
     }
-    const R ir0 = a.inv_rho0;
-    R drho, j[3] = {R(0), R(0), R(0)};
+    const R ir0 = R(a.inv_rho0);
+    R drho, j[3] = {R(0.0f), R(0.0f), R(0.0f)}, u[3] = {R(0.0f), R(0.0f), R(0.0f)};
     R S[NS], tau, snu;
     R out[Q];  // f*_i = f_i - out_i
 
@@ -670,39 +780,40 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
         R m[Q];
         Xf<L>::forward(f[0], P, Dd, m);
         drho = m[0];
-        j[0] = FORCE ? fma(R(0.5), F[0], m[3]) : m[3];
-        j[1] = FORCE ? fma(R(0.5), F[1], m[5]) : m[5];
-        if constexpr (L::D == 3) j[2] = FORCE ? fma(R(0.5), F[2], m[7]) : m[7];
+        j[0] = FORCE ? fma(R(0.5f), F[0], m[3]) : m[3];
+        j[1] = FORCE ? fma(R(0.5f), F[1], m[5]) : m[5];
+        if constexpr (L::D == 3) j[2] = FORCE ? fma(R(0.5f), F[2], m[7]) : m[7];
+        sfor<L::D>([&](auto d) { u[d] = j[d] * ir0; });
         R meq[Q], TF[Q], mn[Q];
-        Eq<L>::meq(drho, j, ir0, meq);
-        if constexpr (FORCE) Eq<L>::tforce(j, F, ir0, TF);
+        Eq<L>::meq(drho, j, u, meq);
+        if constexpr (FORCE) Eq<L>::tforce(u, F, TF);
         sfor<Q>([&](auto k) {
             if constexpr (L::conserved(CV(k)))
-                mn[k] = R(0);
+                mn[k] = R(0.0f);
             else if constexpr (Eq<L>::ghost(CV(k)))
                 mn[k] = m[k];
             else if constexpr (FORCE)
-                mn[k] = fma(R(0.5), TF[k], m[k] - meq[k]);
+                mn[k] = fma(R(0.5f), TF[k], m[k] - meq[k]);
             else
                 mn[k] = m[k] - meq[k];
         });
         R A[NS], B[NS];
-        Eq<L>::yu_split(mn, a.s[1], ir0, A, B);
+        Eq<L>::yu_split(mn, R(a.s[1] * RS(Eq<L>::YU_A)) * ir0, ir0, A, B);
         tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
         if (a.readout) goto readout;
         {
             R Dk[Q];
             sfor<Q>([&](auto k) {
-                constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
+                constexpr double inv_n = 1.0 / norm2<L>(CV(k));
                 if constexpr (L::conserved(CV(k))) {
                     if constexpr (FORCE)
-                        Dk[k] = R(-inv_n) * TF[k];
+                        Dk[k] = cst<R>(-inv_n) * TF[k];
                     else
-                        Dk[k] = R(0);
+                        Dk[k] = R(0.0f);
                 } else {
-                    const R sk = (L::viscous(CV(k)) ? snu : a.s[k]) * inv_n;
+                    const R sk = L::viscous(CV(k)) ? snu * cst<R>(inv_n) : R(a.skn[k]);
                     if constexpr (FORCE && !Eq<L>::ghost(CV(k)))
-                        Dk[k] = fma(sk, mn[k], R(-inv_n) * TF[k]);
+                        Dk[k] = fma(sk, mn[k], cst<R>(-inv_n) * TF[k]);
                     else
                         Dk[k] = sk * mn[k];
                 }
@@ -717,50 +828,55 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
         sfor<L::D>([&](auto d) {
             R acc = nzero<R>();
             sfor<NP>([&](auto p) { acc = cadd<L::c(L::pa(CV(p)), CV(d))>(acc, Dd[p]); });
-            j[d] = FORCE ? fma(R(0.5), F[d], acc) : acc;
+            j[d] = FORCE ? fma(R(0.5f), F[d], acc) : acc;
+            u[d] = j[d] * ir0;
         });
         R fe0, Pe[NP], De[NP], F0, PF[NP], DF[NP];
-        equilibrium_pairs<L, FORCE>(drho, j, F, ir0, fe0, Pe, De, F0, PF, DF);
+        equilibrium_pairs<L, FORCE>(drho, j, u, F, fe0, Pe, De, F0, PF, DF);
         R fn0 = f[0] - fe0, Pn[NP], Dn[NP];
-        if constexpr (FORCE) fn0 = fma(R(0.5), F0, fn0);
+        if constexpr (FORCE) fn0 = fma(R(0.5f), F0, fn0);
         sfor<NP>([&](auto p) {
-            Pn[p] = FORCE ? fma(R(0.5), PF[p], P[p] - Pe[p]) : P[p] - Pe[p];
-            Dn[p] = FORCE ? fma(R(0.5), DF[p], Dd[p] - De[p]) : Dd[p] - De[p];
+            if constexpr (FORCE) {
+                Pn[p] = fma(R(0.5f), PF[p], P[p] - Pe[p]);
+                Dn[p] = fma(R(0.5f), DF[p], Dd[p] - De[p]);
+            } else {
+                Pn[p] = P[p] - Pe[p];
+                Dn[p] = Dd[p] - De[p];
+            }
         });
         R mn[Q];
         Xf<L>::forward(fn0, Pn, Dn, mn);
-        const R kS = R(-1.5) * ir0;  // S = -N / (2 rho0 cs2)
-        R Om[Q];                     // Omega (Newtonian) or its rate-independent part
+        const R kS = R(-1.5f) * ir0;  // S = -N / (2 rho0 cs2)
+        R Om[Q];                       // Omega (Newtonian) or its rate-independent part
         if constexpr (CLOSURE == CL_NEWTON) {
             R Dk[Q];
             sfor<Q>([&](auto k) {
-                constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
                 if constexpr (L::conserved(CV(k)))
-                    Dk[k] = R(0);
+                    Dk[k] = R(0.0f);
                 else
-                    Dk[k] = (a.s[k] * inv_n) * mn[k];
+                    Dk[k] = R(a.skn[k]) * mn[k];
             });
             Xf<L>::template backward<mask_nonconserved<L>()>(Dk, Om);
             R N[NS];
             contract<L>(Om, N);
 #pragma unroll
             for (int c = 0; c < NS; ++c) S[c] = kS * N[c];
-            tau = a.tau0;
-            snu = a.s[L::NU0];
+            tau = R(a.tau0);
+            snu = R(a.s[L::NU0]);
             if (a.readout) goto readout;
             sfor<Q>([&](auto i) { out[i] = Om[i]; });
         } else {
             R Df[Q], Dv[Q];
             sfor<Q>([&](auto k) {
-                constexpr R inv_n = R(1.0 / norm2<L>(CV(k)));
+                constexpr double inv_n = 1.0 / norm2<L>(CV(k));
                 if constexpr (L::conserved(CV(k)) || L::viscous(CV(k)))
-                    Df[k] = R(0);
+                    Df[k] = R(0.0f);
                 else
-                    Df[k] = (a.s[k] * inv_n) * mn[k];
+                    Df[k] = R(a.skn[k]) * mn[k];
                 if constexpr (L::viscous(CV(k)))
-                    Dv[k] = inv_n * mn[k];
+                    Dv[k] = cst<R>(inv_n) * mn[k];
                 else
-                    Dv[k] = R(0);
+                    Dv[k] = R(0.0f);
             });
             R Ov[Q];
             Xf<L>::template backward<mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Om);
@@ -780,25 +896,31 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
         if constexpr (FORCE) {  // f* = f - Omega + Fbar
             out[0] -= F0;
             sfor<NP>([&](auto p) {
-                out[L::pa(CV(p))] -= R(0.5) * (PF[p] + DF[p]);
-                out[L::pb(CV(p))] -= R(0.5) * (PF[p] - DF[p]);
+                out[L::pa(CV(p))] = fma(R(-0.5f), PF[p] + DF[p], out[L::pa(CV(p))]);
+                out[L::pb(CV(p))] = fma(R(-0.5f), PF[p] - DF[p], out[L::pb(CV(p))]);
             });
         }
     }
 
-    sfor<Q>([&](auto i) { Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + node, f[i] - out[i]); });
+    sfor<Q>([&](auto i) {
+        ST* p = static_cast<ST*>(a.dstp[CV(i)]) + node;
+        if constexpr (VW == 2)
+            Store<ST>::st2(p, f[i] - out[i]);
+        else
+            Store<ST>::st(p, f[i] - out[i]);
+    });
     return;
 
 readout:
     if (a.S_out) {
 #pragma unroll
-        for (int c = 0; c < NS; ++c) a.S_out[c * N + node] = S[c];
+        for (int c = 0; c < NS; ++c) store_field(a.S_out + c * N + node, S[c]);
     }
-    if (a.tau_out) a.tau_out[node] = tau;
-    if (a.drho_out) a.drho_out[node] = drho;
+    if (a.tau_out) store_field(a.tau_out + node, tau);
+    if (a.drho_out) store_field(a.drho_out + node, drho);
     if (a.u_out) {
 #pragma unroll
-        for (int d = 0; d < L::D; ++d) a.u_out[d * N + node] = j[d] * ir0;
+        for (int d = 0; d < L::D; ++d) store_field(a.u_out + d * N + node, u[d]);
     }
 }
 
