@@ -195,6 +195,27 @@ int lbm_set_state(lbm_ctx* ctx, const void* src);
 int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_params* p, const double* force,
                      const void* f, int64_t stride, const void* force_field, double* out, void* stream);
 
+/* Gradient of the dissipation functional with respect to the body-force field (adjoint).
+ *
+ *   L(g) = sum_x nu_eff(x) sum_ab S_ab(x)^2,   nu_eff = (tau - 1/2)/3,
+ * with S and tau (closure included) of the pre-collision state that step T+1 would see, after
+ * T steps from the current state under the bound force field F = rho0 g.  dL/dg comes from a
+ * hand-written reverse pass of the full step (Yu-form strain rate, which equals Chai's, Sec. 5.1;
+ * the closure differentiated at its converged fixed point; |S| = 0 contributes no closure term),
+ * with sqrt(T)-style checkpointing: every seg-th state is kept during the forward pass and each
+ * segment is recomputed from its checkpoint during the reverse sweep (about 2T forward steps and
+ * T reverse steps in all).  The force gradient accumulates in the compute type within a segment
+ * and in FP64 across segments.
+ * Supported: D3Q19, LBM_FP32 or LBM_FP64 populations, LBM_NEWTON or LBM_SMAG, all faces
+ * periodic, a force field bound (p->force_field = 1); otherwise LBM_ERR_ARG.
+ *  work     caller-owned device workspace of at least lbm_adjoint_workspace() bytes, 256-byte
+ *           aligned (checkpoints, segment states, two adjoint buffers, accumulators);
+ *  dLdg     device pointer to 3 x N doubles, overwritten with dL/dg (component-major);
+ *  loss     HOST pointer to one double, set to L.
+ * After the call the current buffer holds the state after T steps.  Synchronises the stream. */
+int lbm_adjoint_workspace(lbm_ctx* ctx, int T, int seg, int64_t* bytes);
+int lbm_adjoint(lbm_ctx* ctx, int T, int seg, void* work, int64_t work_bytes, double* dLdg, double* loss);
+
 /* Message of the last failed call on ctx (empty if none), owned by the context.  With ctx = NULL:
  * the message of the last failed lbm_create on the calling thread. */
 const char* lbm_last_error(const lbm_ctx* ctx);

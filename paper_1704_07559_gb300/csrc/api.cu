@@ -9,6 +9,8 @@
 #include <new>
 
 #include "../../include/lbm.h"
+#include "adjoint.cuh"
+#include "adjoint_launch.h"
 #include "launch.h"
 #include "step.cuh"
 
@@ -177,6 +179,150 @@ int check_bound(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
     if (!c->bound) return fail(c, LBM_ERR_STATE, "no buffers bound (call lbm_bind first)");
     return LBM_OK;
+}
+
+
+// ------------------------------------------------------------------------------------------
+// adjoint driver helpers
+
+struct AdjLayout {
+    int ncp = 0, nseg = 0, nblocks = 0;
+    size_t state = 0, lam = 0, dF = 0, partial = 0;
+    size_t off_cp = 0, off_seg = 0, off_lam = 0, off_dF = 0, off_partial = 0, total = 0;
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int adjoint_check(lbm_ctx* c, int T, int seg) {
+    if (c->q != 19) return fail(c, LBM_ERR_ARG, "lbm_adjoint: D3Q19 only");
+    if (c->p.precision != LBM_FP32 && c->p.precision != LBM_FP64)
+        return fail(c, LBM_ERR_ARG, "lbm_adjoint: FP32 or FP64 populations only");
+    if (c->p.closure != LBM_NEWTON && c->p.closure != LBM_SMAG)
+        return fail(c, LBM_ERR_ARG, "lbm_adjoint: Newtonian or Smagorinsky closure only");
+    for (int f = 0; f < 6; ++f)
+        if (c->p.bc[f] != LBM_PERIODIC) return fail(c, LBM_ERR_ARG, "lbm_adjoint: periodic faces only");
+    if (!c->p.force_field) return fail(c, LBM_ERR_ARG, "lbm_adjoint: needs a bound force field (the gradient's variable)");
+    if (T < 0 || seg < 1) return fail(c, LBM_ERR_ARG, "lbm_adjoint: T >= 0 and seg >= 1 required");
+    return LBM_OK;
+}
+
+AdjLayout adjoint_layout(const lbm_ctx* c, int T, int seg) {
+    AdjLayout L;
+    const size_t comp = c->p.precision == LBM_FP64 ? 8 : 4;
+    L.ncp = T > 0 ? (T + seg - 1) / seg : 0;
+    L.nseg = T > 0 ? (seg < T ? seg : T) - 1 : 0;
+    L.nblocks = lbm::functional_blocks(c->nx, c->ny, c->nz);
+    L.state = align256((size_t)c->q * c->stride * c->elem_bytes);
+    L.lam = align256((size_t)c->q * c->stride * comp);
+    L.dF = align256((size_t)3 * c->N * comp);
+    L.partial = align256((size_t)(L.nblocks + 1) * sizeof(double));
+    L.off_cp = 0;
+    L.off_seg = L.off_cp + L.ncp * L.state;
+    L.off_lam = L.off_seg + L.nseg * L.state;
+    L.off_dF = L.off_lam + 2 * L.lam;
+    L.off_partial = L.off_dF + L.dF;
+    L.total = L.off_partial + L.partial;
+    return L;
+}
+
+template <class R>
+cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout& L, double* dLdg, double* loss) {
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    const size_t state_bytes = (size_t)c->q * c->stride * c->elem_bytes;
+    auto cp = [&](int k) { return static_cast<void*>(work + L.off_cp + k * L.state); };
+    auto sg = [&](int k) { return static_cast<void*>(work + L.off_seg + k * L.state); };
+    R* lam[2] = {reinterpret_cast<R*>(work + L.off_lam), reinterpret_cast<R*>(work + L.off_lam + L.lam)};
+    R* dF = reinterpret_cast<R*>(work + L.off_dF);
+    double* partial = reinterpret_cast<double*>(work + L.off_partial);
+    double* result = partial + L.nblocks;
+    constexpr bool F64 = std::is_same<R, double>::value;
+    auto fold = [&](R* acc) {
+        if constexpr (F64)
+            return lbm::adj_fold_f64(acc, dLdg, c->p.rho0, 3LL * c->N, s);
+        else
+            return lbm::adj_fold_f32(acc, dLdg, c->p.rho0, 3LL * c->N, s);
+    };
+
+    // forward T steps from the current state, keeping every seg-th state
+    const void* fcur = c->buf[c->cur];
+    if (T > 0) {
+        e = cudaMemcpyAsync(cp(0), c->buf[c->cur], state_bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        fcur = cp(0);
+        int other = c->cur;  // ping-pong through the context's two buffers
+        for (int n = 0; n < T; ++n) {
+            void* dst;
+            if ((n + 1) % seg == 0 && n + 1 < T) {
+                dst = cp((n + 1) / seg);
+            } else {
+                other = (fcur == c->buf[other]) ? 1 - other : other;
+                dst = c->buf[other];
+            }
+            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, fcur, dst);
+            if (e != cudaSuccess) return e;
+            fcur = dst;
+        }
+        if (fcur != c->buf[0] && fcur != c->buf[1]) {
+            e = cudaMemcpyAsync(c->buf[c->cur], fcur, state_bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            fcur = c->buf[c->cur];
+        }
+        c->cur = fcur == c->buf[0] ? 0 : 1;
+    }
+
+    lbm::AdjArgs<R> a;
+    fill_args(c, &a.st);
+    a.dF = dF;
+    a.partial = partial;
+    // the functional at f^T: loss partials, lambda_T, dF
+    set_buffers(c, &a.st, fcur, nullptr);
+    a.lam_in = nullptr;
+    a.lam_out = lam[0];
+    int nb = 0;
+    if constexpr (F64)
+        e = lbm::adj_functional_f64(a, c->p.closure, s, &nb);
+    else
+        e = lbm::adj_functional_f32(a, c->p.closure, s, &nb);
+    if (e != cudaSuccess) return e;
+    lbm::k_sums_final<<<1, 256, 0, s>>>(partial, nb, 1, result);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(dLdg, 0, sizeof(double) * 3 * c->N, s);
+    if (e != cudaSuccess) return e;
+
+    // reverse sweep, segment by segment from the last, recomputing each segment's states
+    int lc = 0;
+    for (int sgi = L.ncp - 1; sgi >= 0; --sgi) {
+        const int k0 = sgi * seg, k1 = (k0 + seg < T) ? k0 + seg : T;
+        const void* states[1024];
+        states[0] = cp(sgi);
+        for (int i = 1; i < k1 - k0; ++i) {
+            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, states[i - 1], sg(i - 1));
+            if (e != cudaSuccess) return e;
+            states[i] = sg(i - 1);
+        }
+        for (int n = k1 - 1; n >= k0; --n) {
+            set_buffers(c, &a.st, states[n - k0], nullptr);
+            a.lam_in = lam[lc];
+            a.lam_out = lam[1 - lc];
+            if constexpr (F64)
+                e = lbm::adj_step_f64(a, c->p.closure, s);
+            else
+                e = lbm::adj_step_f32(a, c->p.closure, s);
+            if (e != cudaSuccess) return e;
+            lc = 1 - lc;
+        }
+        e = fold(dF);
+        if (e != cudaSuccess) return e;
+    }
+    if (L.ncp == 0) {  // T = 0: only the functional's direct term
+        e = fold(dF);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemcpyAsync(loss, result, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
 }
 
 }  // namespace
@@ -468,5 +614,32 @@ int lbm_set_state(lbm_ctx* c, const void* src) {
 }
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : create_err; }
+
+int lbm_adjoint_workspace(lbm_ctx* c, int T, int seg, int64_t* bytes) {
+    if (!c || !bytes) return LBM_ERR_ARG;
+    int rc = adjoint_check(c, T, seg);
+    if (rc) return rc;
+    if (seg > 1024) return fail(c, LBM_ERR_ARG, "lbm_adjoint: seg <= 1024");
+    *bytes = (int64_t)adjoint_layout(c, T, seg).total;
+    return LBM_OK;
+}
+
+int lbm_adjoint(lbm_ctx* c, int T, int seg, void* work, int64_t work_bytes, double* dLdg, double* loss) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    rc = adjoint_check(c, T, seg);
+    if (rc) return rc;
+    if (seg > 1024) return fail(c, LBM_ERR_ARG, "lbm_adjoint: seg <= 1024");
+    if (!work || !dLdg || !loss) return fail(c, LBM_ERR_ARG, "lbm_adjoint: work, dLdg and loss are required");
+    if ((uintptr_t)work & 255) return fail(c, LBM_ERR_ARG, "lbm_adjoint: workspace must be 256-byte aligned");
+    const AdjLayout L = adjoint_layout(c, T, seg);
+    if (work_bytes < (int64_t)L.total) return fail(c, LBM_ERR_ARG, "lbm_adjoint: workspace too small");
+    cudaError_t e = c->p.precision == LBM_FP64
+                        ? adjoint_run<double>(c, T, seg, static_cast<char*>(work), L, dLdg, loss)
+                        : adjoint_run<float>(c, T, seg, static_cast<char*>(work), L, dLdg, loss);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint");
+    if (!is_finite(*loss)) return fail(c, LBM_ERR_NONFINITE, "lbm_adjoint: non-finite functional");
+    return LBM_OK;
+}
 
 }  // extern "C"

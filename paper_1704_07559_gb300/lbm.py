@@ -26,7 +26,7 @@ STORAGE_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_STATE"}
 API = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_layout", "lbm_bind", "lbm_init", "lbm_step",
        "lbm_strain_rate", "lbm_macroscopic", "lbm_sums", "lbm_get_state", "lbm_set_state", "lbm_last_error",
-       "lbm_sums_noalloc"]
+       "lbm_sums_noalloc", "lbm_adjoint_workspace", "lbm_adjoint"]
 
 
 class LBMError(RuntimeError):
@@ -83,6 +83,8 @@ def lib():
     L.lbm_sums.argtypes = [vp, dp]
     L.lbm_get_state.argtypes = [vp, vp]
     L.lbm_set_state.argtypes = [vp, vp]
+    L.lbm_adjoint_workspace.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_adjoint.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int64, vp, dp]
     L.lbm_last_error.argtypes = [vp]
     L.lbm_last_error.restype = ctypes.c_char_p
     for name in API:
@@ -231,9 +233,44 @@ class Lattice:
         self._check(lib().lbm_get_state(self.ctx, _ptr(out)))
         return out
 
+    def adjoint(self, T, seg=None):
+        """(L, dL/dg) after T steps from the current state: L as a float, dL/dg as a float64
+        tensor (d, nz, ny, nx).  seg defaults to round(sqrt(T)).  The current state afterwards is
+        the state after T steps."""
+        seg = int(seg or max(1, round(T ** 0.5)))
+        L = lib()
+        nbytes = ctypes.c_int64()
+        self._check(L.lbm_adjoint_workspace(self.ctx, int(T), seg, ctypes.byref(nbytes)))
+        work = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        off = (-work.data_ptr()) % 256
+        grad = torch.empty((self.d,) + self.shape, dtype=torch.float64, device=self.device)
+        loss = ctypes.c_double()
+        self._check(L.lbm_adjoint(self.ctx, int(T), seg, ctypes.c_void_p(work.data_ptr() + off), nbytes.value,
+                                  _ptr(grad), ctypes.byref(loss)))
+        return loss.value, grad
+
     def set_state(self, f):
         f = f.to(dtype=self.storage_dtype).contiguous()
         assert f.numel() == self.q * self.N
         self._check(lib().lbm_set_state(self.ctx, _ptr(f)))
         self._keep = f
         return self
+
+
+class DissipationLoss(torch.autograd.Function):
+    """L(g): the dissipation functional after T steps from the state f0 under the force field g
+    (bound to `lat`, which must have been created with a force field).  Forward runs the steps and
+    the library's adjoint together; backward returns grad_output * dL/dg."""
+
+    @staticmethod
+    def forward(ctx, g, lat, f0, T, seg=None):
+        lat.force_field.copy_(g.detach().to(lat.force_field.dtype).reshape(lat.force_field.shape))
+        lat.set_state(f0)
+        loss, grad = lat.adjoint(T, seg)
+        ctx.save_for_backward(grad.to(g.dtype).reshape(g.shape))
+        return torch.tensor(loss, dtype=torch.float64, device=g.device)
+
+    @staticmethod
+    def backward(ctx, grad_output):
+        (grad,) = ctx.saved_tensors
+        return grad_output.to(grad.dtype) * grad, None, None, None, None
