@@ -281,23 +281,185 @@ def run_ours(args):
 
 
 def variants(args, hbm):
-    """The other (formula x form) pairs on the same channel, same timing protocol."""
+    """The other (formula x form) pairs and the other workloads, each with its own timing."""
     import torch
 
-    res = {}
+    res = {"channel": {}}
     steps = max(10, min(args.steps, 1000))
+    # channel (headline workload): the other formula x precision pairs
     for precision, formula in (("fp32", "chai"), ("fp16s", "yu"), ("fp16s", "chai"), ("bf16s", "yu"),
                                ("bf16s", "chai"), ("fp64", "yu"), ("fp64", "chai")):
         lat = make_lattice(precision, formula)
         n = steps if precision != "fp64" else max(5, steps // 10)
-        per = time_steps(lat, n, max(3, args.warmup // 10), per_launch=True)
-        k_ms = statistics.mean(per)
-        gbs = BYTES_PER_LUP[precision] * lat.N / (k_ms * 1e-3) / 1e9
-        res["%s_%s" % (precision, formula)] = {"MLUPS": round(lat.N / (k_ms * 1e-3) / 1e6, 1),
-                                              "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4)}
+        k_ms = statistics.mean(time_steps(lat, n, max(3, args.warmup // 10), per_launch=True))
+        res["channel"]["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
         lat.close()
         torch.cuda.empty_cache()
+    for name, fn in (("box512", box512), ("precision64", precision64), ("cavity4096", cavity4096),
+                     ("adjoint128", adjoint128), ("tgv32", tgv32)):
+        try:
+            res[name] = fn(args, hbm)
+        except Exception as e:  # report, keep the headline line
+            res[name] = {"error": repr(e)[:300]}
+        torch.cuda.empty_cache()
     return res
+
+
+def rate(N, k_ms, bytes_per_lup, hbm):
+    gbs = bytes_per_lup * N / (k_ms * 1e-3) / 1e9
+    return {"MLUPS": round(N / (k_ms * 1e-3) / 1e6, 1), "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
+            "kernel_ms": round(k_ms, 5)}
+
+
+def box_lattice(n, precision, formula, kmax, rms, seed, with_force=None, closure="smag"):
+    from paper_1704_07559_gb300 import inputs as I
+    from paper_1704_07559_gb300 import lbm
+
+    kw = {}
+    if with_force is not None:
+        kw["force_field"] = with_force
+    lat = lbm.Lattice(lbm.D3Q19, n, n, n, rates=RATES, precision=precision, closure=closure, smag_cs=CS,
+                      formula=formula, **kw)
+    drho, u = I.random_fourier(n, n, n, kmax=kmax, rms=rms, seed=seed, device="cuda")
+    lat.init(drho, u)
+    del drho, u
+    return lat
+
+
+def box512(args, hbm):
+    """Reduced-precision workload: 512^3 periodic Smagorinsky box, divergence-free random Fourier
+    start (|k| <= 8, rms 0.03, seed 4); FP32, FP16S and BF16S storage, both routes."""
+    import torch
+
+    out = {}
+    n = 512
+    for precision in ("fp32", "fp16s", "bf16s"):
+        for formula in ("yu", "chai"):
+            lat = box_lattice(n, precision, formula, 8, 0.03, 4)
+            k_ms = statistics.mean(time_steps(lat, 30, 5, per_launch=True))
+            out["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
+            lat.close()
+            torch.cuda.empty_cache()
+    return out
+
+
+def precision64(args, hbm):
+    """Error of FP32 / FP16S / BF16S storage against FP64 on a 64^3 instance of the same field:
+    relative L2 and max errors of u and S after 100 and 1000 steps (the FP64 path itself matches
+    the FP64 oracle to 1e-12 per step, checked by the parity tests)."""
+    out = {}
+    n = 64
+    ref = box_lattice(n, "fp64", "yu", 8, 0.03, 4)
+    lats = {p: box_lattice(n, p, "yu", 8, 0.03, 4) for p in ("fp32", "fp16s", "bf16s")}
+    done = 0
+    for mark in (100, 1000):
+        ref.step(mark - done)
+        for lat in lats.values():
+            lat.step(mark - done)
+        done = mark
+        _, ur = ref.macroscopic()
+        Sr = ref.strain_rate("yu")
+        for p, lat in lats.items():
+            _, u = lat.macroscopic()
+            S = lat.strain_rate("yu")
+            eu, eS = u.double() - ur, S.double() - Sr
+            out["%s_t%d" % (p, mark)] = {
+                "u_rel_l2": float(eu.norm() / ur.norm()), "u_rel_max": float(eu.abs().max() / ur.abs().max()),
+                "S_rel_l2": float(eS.norm() / Sr.norm()), "S_rel_max": float(eS.abs().max() / Sr.abs().max())}
+    for lat in [ref] + list(lats.values()):
+        lat.close()
+    return out
+
+
+def cavity4096(args, hbm):
+    """D2Q9 power-law lid-driven cavity, 4096^2, lid velocity 0.05, n in {0.5, 1, 1.5}, consistency
+    K = U^(2-n) L^n / Re with Re = 1000, tau solved per node by fixed point, fluid at rest at t = 0."""
+    from paper_1704_07559_gb300 import lbm
+
+    out = {}
+    Lc, U, Re = 4096, 0.05, 1000.0
+    tau_ref = 0.5 + 3 * U * Lc / Re
+    r9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / tau_ref, 1 / tau_ref]
+    for nidx in (0.5, 1.0, 1.5):
+        K = U ** (2 - nidx) * Lc ** nidx / Re
+        for formula in ("chai", "yu"):
+            lat = lbm.Lattice(lbm.D2Q9, Lc, Lc, 1, rates=r9, precision="fp32", closure="powerlaw", formula=formula,
+                              pl_n=nidx, pl_k=K, pl_tau_min=0.505, pl_tau_max=5.0, bc=["wall", "wall", "wall", "lid"],
+                              lid_u={3: (U, 0.0, 0.0)})
+            import torch
+
+            lat.init(torch.zeros((1, Lc, Lc), dtype=torch.float64, device="cuda"),
+                     torch.zeros((2, 1, Lc, Lc), dtype=torch.float64, device="cuda"))
+            k_ms = statistics.mean(time_steps(lat, 50, 20, per_launch=True))
+            out["n%.1f_%s" % (nidx, formula)] = rate(lat.N, k_ms, 72, hbm)
+            lat.close()
+    return out
+
+
+def adjoint128(args, hbm):
+    """Adjoint workload: 128^3 periodic Smagorinsky box, force field N(0, (1e-5)^2) (seed 5),
+    start from the random Fourier field |k| <= 4, rms 0.01 (seed 6); dL/dg of the dissipation
+    after T = 256 steps with checkpoints every 16 steps.  Reports the forward time of T steps, the
+    time of lbm_adjoint (forward with checkpoints + functional + reverse sweep with recompute),
+    and their ratio."""
+    import torch
+    from paper_1704_07559_gb300 import inputs as I
+
+    n, T, seg = 128, 256, 16
+    g = torch.from_numpy(I.gaussian_force(3, (n, n, n), std=1e-5, seed=5))
+    lat = box_lattice(n, "fp32", "yu", 4, 0.01, 6, with_force=g)
+    f0 = lat.get_state().clone()
+    lat.step(5)
+    torch.cuda.synchronize()
+    s = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fwd = []
+    for _ in range(3):
+        lat.set_state(f0)
+        e0.record(s)
+        lat.step(T)
+        e1.record(s)
+        torch.cuda.synchronize()
+        fwd.append(e0.elapsed_time(e1))
+    lat.set_state(f0)
+    lat.adjoint(T, seg)  # warm-up
+    adj = []
+    for _ in range(3):
+        lat.set_state(f0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, grad = lat.adjoint(T, seg)
+        adj.append((time.perf_counter() - t0) * 1e3)
+    f_ms, a_ms = min(fwd), min(adj)
+    lat.close()
+    return {"T": T, "seg": seg, "loss": loss, "grad_rms": float(grad.pow(2).mean().sqrt()),
+            "forward_ms": round(f_ms, 3), "adjoint_total_ms": round(a_ms, 3),
+            "reverse_over_forward": round((a_ms - f_ms) / f_ms, 3), "total_over_forward": round(a_ms / f_ms, 3)}
+
+
+def tgv32(args, hbm):
+    """Correctness workload: D3Q19 FP64, 32^3 periodic Taylor-Green vortex u0 = 0.02, tau = 0.6,
+    500 steps; S by Yu and by Chai, their difference, and the decay of S against the linear
+    (Stokes) rate exp(-3 nu k^2 t) of this non-exact flow."""
+    from paper_1704_07559_gb300 import inputs as I
+    from paper_1704_07559_gb300 import lbm
+
+    n, u0, tau, T = 32, 0.02, 0.6, 500
+    r = list(RATES)
+    for k in (9, 11, 13, 14, 15):
+        r[k] = 1 / tau
+    lat = lbm.Lattice(lbm.D3Q19, n, n, n, rates=r, precision="fp64", closure="newton")
+    drho, u, g = I.taylor_green_3d(n, u0=u0)
+    lat.init(drho, u, g)
+    S0 = lat.strain_rate("yu").abs().max().item()
+    k_ms = statistics.mean(time_steps(lat, T, 0, per_launch=True))
+    Sy, Sc = lat.strain_rate("yu"), lat.strain_rate("chai")
+    nu, kk = (tau - 0.5) / 3, 2 * np.pi / n
+    ratio = Sy.abs().max().item() / S0 / np.exp(-3 * nu * kk * kk * T)
+    lat.close()
+    return {"steps": T, "MLUPS": round(n ** 3 / (k_ms * 1e-3) / 1e6, 1),
+            "yu_minus_chai_rel": float((Sy - Sc).abs().max() / Sy.abs().max()),
+            "S_amplitude_over_stokes_decay": round(ratio, 5)}
 
 
 # ------------------------------------------------------------------------------------------------

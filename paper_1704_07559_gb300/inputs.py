@@ -90,28 +90,34 @@ def abc_flow(n, u0=0.02):
     return np.zeros_like(x), u, g
 
 
-def random_fourier(nx, ny, nz, kmax=8, rms=0.03, seed=4):
+def random_fourier(nx, ny, nz, kmax=8, rms=0.03, seed=4, device=None):
     """Divergence-free random velocity field: Fourier modes with 0 < |k| <= kmax (integer
     wavevectors of the periodic box), unit-variance complex Gaussian amplitudes projected onto
-    the plane normal to k, transformed to real space and scaled to the requested rms speed
-    (rms of |u| over the box).  The same seed gives the same field at every grid size whose
-    Nyquist limit exceeds kmax.  Returns drho (zero), u (3 fields)."""
+    the plane normal to k, summed in real space (the real part of sum_k a_k exp(i k.x)) and
+    scaled to the requested rms speed (rms of |u| over the box).  The same seed gives the same
+    field at every grid size whose Nyquist limit exceeds kmax.  The sum is evaluated as an
+    inverse FFT of the mode amplitudes, on the CPU (numpy) or, with device set, on that torch
+    device (returned as torch tensors there).  Returns drho (zero), u (3 fields)."""
     K, amp = random_fourier_modes(kmax, seed)
-    # the real part of the mode sum is real-valued and stays divergence free
-    u = np.zeros((3, nz, ny, nx))
-    x = np.arange(nx) * 2 * np.pi / nx
-    y = np.arange(ny) * 2 * np.pi / ny
-    z = np.arange(nz) * 2 * np.pi / nz
-    for (kx, ky, kz), a in zip(K, amp):
-        ex = np.exp(1j * kx * x)[None, None, :]
-        ey = np.exp(1j * ky * y)[None, :, None]
-        ez = np.exp(1j * kz * z)[:, None, None]
-        phase = ez * ey * ex
-        for c in range(3):
-            u[c] += np.real(a[c] * phase)
-    speed_rms = np.sqrt((u * u).sum(0).mean())
-    u *= rms / speed_rms
-    return np.zeros((nz, ny, nx)), u
+    assert min(nx, ny, nz) > 2 * kmax, "grid too small for the requested modes"
+    if device is None:
+        spec = np.zeros((3, nz, ny, nx), dtype=np.complex128)
+        for (kx, ky, kz), a in zip(K, amp):
+            spec[:, kz % nz, ky % ny, kx % nx] += a
+        u = np.real(np.fft.ifftn(spec, axes=(1, 2, 3))) * (nx * ny * nz)
+        speed_rms = np.sqrt((u * u).sum(0).mean())
+        return np.zeros((nz, ny, nx)), u * (rms / speed_rms)
+    import torch
+
+    spec = torch.zeros((3, nz, ny, nx), dtype=torch.complex128, device=device)
+    idx = torch.tensor(np.stack([K[:, 2] % nz, K[:, 1] % ny, K[:, 0] % nx], axis=1), device=device)
+    vals = torch.tensor(amp, dtype=torch.complex128, device=device)
+    for c in range(3):
+        spec[c].index_put_((idx[:, 0], idx[:, 1], idx[:, 2]), vals[:, c], accumulate=True)
+    u = torch.fft.ifftn(spec, dim=(1, 2, 3)).real * (nx * ny * nz)
+    del spec
+    speed_rms = torch.sqrt((u * u).sum(0).mean())
+    return torch.zeros((nz, ny, nx), dtype=torch.float64, device=device), u * (rms / speed_rms)
 
 
 def random_fourier_modes(kmax=8, seed=4):
