@@ -52,6 +52,25 @@ def env_int(name, default):
         return default
 
 
+def captured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the capture
+    is of another kernel or the kernel sources changed since it was taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as fh:
+            doc = json.load(fh)
+        h = hashlib.sha256()
+        for src in doc["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                h.update(fh.read())
+        if doc["kernel"] == kernel and h.hexdigest() == doc["sources_sha256"]:
+            return int(doc["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -246,6 +265,7 @@ def run_ours(args):
     k_ms = statistics.mean(per)
     achieved = BYTES_PER_LUP[args.precision] * N / (k_ms * 1e-3) / 1e9
 
+    kernel = "k_step<D3Q19,%s,SMAG,%s,force>" % (args.precision, args.formula.upper())
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
@@ -255,8 +275,9 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (two 319 MB population buffers per step)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_step<D3Q19,%s,SMAG,%s,force>" % (args.precision, args.formula.upper()),
+                     "frac": round(achieved / hbm, 4),
+                     "traffic": captured_traffic(kernel) if args.precision == "fp32" and args.formula == "yu" else None,
+                     "peak_kind": peak_kind, "kernel": kernel,
                      "bytes_per_lup": BYTES_PER_LUP[args.precision],
                      "kernel_ms": round(k_ms, 5)},
         "gpu_launches": args.steps,
