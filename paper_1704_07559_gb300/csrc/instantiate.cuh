@@ -4,38 +4,79 @@
 
 #include "launch.h"
 #include "step.cuh"
+#include "step_async.cuh"
 
 namespace lbm {
 
-// The packed two-node form (VW = 2: float compute, nx even so each thread's pair is 8-byte
-// aligned) executes about 0.63x the instructions of the one-node form but needs ~140 registers,
-// and at that occupancy it is latency-bound and no faster on GB300; it is compiled out until the
-// loads are decoupled from the registers.  One node per thread is dispatched.
-constexpr bool kDispatchPairs = false;
+// Step kernel selection for the float compute types (FP32, FP16S, BF16S):
+//   LBM_STEP_FORM 0: one node per thread, direct loads (k_step, VW = 1);
+//   LBM_STEP_FORM 1: persistent double-buffered k_step_async, one node per thread;
+//   LBM_STEP_FORM 2: persistent double-buffered k_step_async, two nodes per thread in packed
+//                    FP32 pairs when nx is even (one node per thread otherwise);
+//   LBM_STEP_FORM 3: persistent k_step_prefetch (next node's loads in registers), one node;
+//   LBM_STEP_FORM 4: persistent k_step_prefetch, two nodes per thread when nx is even;
+//   LBM_STEP_FORM 5: k_step with two nodes per thread in packed FP32 pairs when nx is even.
+// FP64 always uses k_step (its arithmetic, not its loads, bounds it).
+#ifndef LBM_STEP_FORM
+#define LBM_STEP_FORM 0
+#endif
+
 template <class ST>
-constexpr bool has_pairs() {
-    return kDispatchPairs && std::is_same<typename Store<ST>::R, float>::value;
+constexpr bool float_compute() {
+    return std::is_same<typename Store<ST>::R, float>::value;
+}
+
+template <class L, class ST, int C, int F, bool FO, int VW, bool PREFETCH>
+cudaError_t launch_async(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
+    const int nseg = (a.nx + ASYNC_THREADS * VW - 1) / (ASYNC_THREADS * VW);
+    const long long tiles = (long long)nseg * a.ny * a.nz;
+    const int smem = PREFETCH ? 0 : 2 * L::Q * ASYNC_THREADS * slot_bytes<ST, VW>();
+    static int per_sm = 0, sms = 0;  // occupancy of this instantiation, found once
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (PREFETCH)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_prefetch<L, ST, C, F, FO, VW>, ASYNC_THREADS, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_async<L, ST, C, F, FO, VW>, ASYNC_THREADS, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long want = (long long)per_sm * sms;
+    const int grid = (int)(tiles < want ? tiles : want);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if constexpr (PREFETCH)
+        k_step_prefetch<L, ST, C, F, FO, VW><<<grid, ASYNC_THREADS, 0, s>>>(a, nseg, (int)tiles);
+    else
+        k_step_async<L, ST, C, F, FO, VW><<<grid, ASYNC_THREADS, smem, s>>>(a, nseg, (int)tiles);
+    return cudaGetLastError();
+}
+
+template <class L, class ST, int C, int F, bool FO>
+cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
+    if constexpr (float_compute<ST>() && LBM_STEP_FORM != 0) {
+        if (LBM_STEP_FORM == 5 && !a.readout && a.nx % 2 == 0) {
+            dim3 g, b;
+            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
+            k_step<L, ST, C, F, FO, 2><<<g, b, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        if (LBM_STEP_FORM != 5 && !a.readout) {
+            constexpr bool PF = LBM_STEP_FORM >= 3;
+            constexpr bool PAIRS = LBM_STEP_FORM == 2 || LBM_STEP_FORM == 4;
+            if (PAIRS && a.nx % 2 == 0) return launch_async<L, ST, C, F, FO, 2, PF>(a, s);
+            return launch_async<L, ST, C, F, FO, 1, PF>(a, s);
+        }
+    }
+    dim3 g, b;
+    lattice_grid(a.nx, a.ny, a.nz, &g, &b);
+    k_step<L, ST, C, F, FO, 1><<<g, b, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <class L, class ST, int C, int F>
 cudaError_t launch_step_cf(const StepArgs<typename Store<ST>::R>& a, int force, cudaStream_t s) {
-    dim3 g, b;
-    if constexpr (has_pairs<ST>()) {
-        if (a.nx % 2 == 0) {
-            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
-            if (force)
-                k_step<L, ST, C, F, true, 2><<<g, b, 0, s>>>(a);
-            else
-                k_step<L, ST, C, F, false, 2><<<g, b, 0, s>>>(a);
-            return cudaGetLastError();
-        }
-    }
-    lattice_grid(a.nx, a.ny, a.nz, &g, &b);
-    if (force)
-        k_step<L, ST, C, F, true, 1><<<g, b, 0, s>>>(a);
-    else
-        k_step<L, ST, C, F, false, 1><<<g, b, 0, s>>>(a);
-    return cudaGetLastError();
+    return force ? launch_form<L, ST, C, F, true>(a, s) : launch_form<L, ST, C, F, false>(a, s);
 }
 
 template <class L, class ST, bool POWERLAW_BUILT>

@@ -739,23 +739,17 @@ __device__ __forceinline__ void store_field(RS* p, R v) {
         *p = v;
 }
 
+// Everything of a step after the pull, for the node(s) starting at `node`: moments, strain rate
+// by the chosen route, closure, relaxation, force, and either the store of f* or (readout) the
+// store of S, tau, drho and u.
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
-__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
+__device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>& a,
+                                          std::conditional_t<VW == 2, F2, typename Store<ST>::R> (&f)[L::Q],
+                                          int node) {
     using RS = typename Store<ST>::R;
     using R = std::conditional_t<VW == 2, F2, RS>;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
-    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= a.nx || y >= a.ny) return;
     const int N = a.nx * a.ny * a.nz;
-    const int node = (z * a.ny + y) * a.nx + x;
-
-    R f[Q];
-    if constexpr (VW == 2)
-        pull2<L, ST>(a, x, y, z, f);
-    else
-        pull<L, ST>(a, x, y, z, f);
 
     R P[NP], Dd[NP];
     sfor<NP>([&](auto p) {
@@ -784,42 +778,56 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
         j[1] = FORCE ? fma(R(0.5f), F[1], m[5]) : m[5];
         if constexpr (L::D == 3) j[2] = FORCE ? fma(R(0.5f), F[2], m[7]) : m[7];
         sfor<L::D>([&](auto d) { u[d] = j[d] * ir0; });
-        R meq[Q], TF[Q], mn[Q];
-        Eq<L>::meq(drho, j, u, meq);
-        if constexpr (FORCE) Eq<L>::tforce(u, F, TF);
-        sfor<Q>([&](auto k) {
-            if constexpr (L::conserved(CV(k)))
-                mn[k] = R(0.0f);
-            else if constexpr (Eq<L>::ghost(CV(k)))
-                mn[k] = m[k];
-            else if constexpr (FORCE)
-                mn[k] = fma(R(0.5f), TF[k], m[k] - meq[k]);
-            else
-                mn[k] = m[k] - meq[k];
-        });
-        R A[NS], B[NS];
-        Eq<L>::yu_split(mn, R(a.s[1] * RS(Eq<L>::YU_A)) * ir0, ir0, A, B);
-        tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
-        if (a.readout) goto readout;
+        // non-equilibrium moments; every collision increment D_k that does not involve the unknown
+        // viscous rate is finished before the closure, so only the viscous moments (and their force
+        // terms) stay live across the fixed point
+        R Dk[Q], mn[Q], tv[Q];
         {
-            R Dk[Q];
+            R meq[Q], TF[Q];
+            Eq<L>::meq(drho, j, u, meq);
+            if constexpr (FORCE) Eq<L>::tforce(u, F, TF);
             sfor<Q>([&](auto k) {
                 constexpr double inv_n = 1.0 / norm2<L>(CV(k));
                 if constexpr (L::conserved(CV(k))) {
+                    mn[k] = R(0.0f);
                     if constexpr (FORCE)
                         Dk[k] = cst<R>(-inv_n) * TF[k];
                     else
                         Dk[k] = R(0.0f);
                 } else {
-                    const R sk = L::viscous(CV(k)) ? snu * cst<R>(inv_n) : R(a.skn[k]);
-                    if constexpr (FORCE && !Eq<L>::ghost(CV(k)))
-                        Dk[k] = fma(sk, mn[k], cst<R>(-inv_n) * TF[k]);
+                    if constexpr (Eq<L>::ghost(CV(k)))
+                        mn[k] = m[k];
+                    else if constexpr (FORCE)
+                        mn[k] = fma(R(0.5f), TF[k], m[k] - meq[k]);
                     else
-                        Dk[k] = sk * mn[k];
+                        mn[k] = m[k] - meq[k];
+                    const bool has_tf = FORCE && !Eq<L>::ghost(CV(k));
+                    if constexpr (L::viscous(CV(k))) {
+                        tv[k] = has_tf ? cst<R>(-inv_n) * TF[k] : R(0.0f);
+                    } else {
+                        if constexpr (FORCE && !Eq<L>::ghost(CV(k)))
+                            Dk[k] = fma(R(a.skn[k]), mn[k], cst<R>(-inv_n) * TF[k]);
+                        else
+                            Dk[k] = R(a.skn[k]) * mn[k];
+                    }
                 }
             });
-            Xf<L>::template backward<FORCE ? mask_all_but_density<L>() : mask_nonconserved<L>()>(Dk, out);
         }
+        R A[NS], B[NS];
+        Eq<L>::yu_split(mn, R(a.s[1] * RS(Eq<L>::YU_A)) * ir0, ir0, A, B);
+        tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
+        if (a.readout) goto readout;
+        sfor<Q>([&](auto k) {
+            if constexpr (L::viscous(CV(k))) {
+                constexpr double inv_n = 1.0 / norm2<L>(CV(k));
+                if constexpr (FORCE)
+                    Dk[k] = fma(snu * cst<R>(inv_n), mn[k], tv[k]);
+                else
+                    Dk[k] = (snu * cst<R>(inv_n)) * mn[k];
+            }
+        });
+        // with a force, the conserved moments 3, 5, 7 (D2Q9: 3, 5) carry -TF_k; TF_0 = 0
+        Xf<L>::template backward<FORCE ? mask_all_but_density<L>() : mask_nonconserved<L>()>(Dk, out);
     } else {
         // Chai route: non-equilibrium distributions f - f_eq + Fbar/2 (in opposite-pair form), the
         // collision operator T^-1 L T applied to them, and the second velocity moment of the result
@@ -922,6 +930,22 @@ readout:
 #pragma unroll
         for (int d = 0; d < L::D; ++d) store_field(a.u_out + d * N + node, u[d]);
     }
+}
+
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
+__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
+    using RS = typename Store<ST>::R;
+    using R = std::conditional_t<VW == 2, F2, RS>;
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    R f[L::Q];
+    if constexpr (VW == 2)
+        pull2<L, ST>(a, x, y, z, f);
+    else
+        pull<L, ST>(a, x, y, z, f);
+    step_body<L, ST, CLOSURE, FORMULA, FORCE, VW>(a, f, (z * a.ny + y) * a.nx + x);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -93,13 +93,14 @@ def abc_flow(n, u0=0.02):
 def random_fourier(nx, ny, nz, kmax=8, rms=0.03, seed=4, device=None):
     """Divergence-free random velocity field: Fourier modes with 0 < |k| <= kmax (integer
     wavevectors of the periodic box), unit-variance complex Gaussian amplitudes projected onto
-    the plane normal to k, summed in real space (the real part of sum_k a_k exp(i k.x)) and
+    the plane normal to k, summed on the grid points (the real part of sum_k a_k exp(i k.x)) and
     scaled to the requested rms speed (rms of |u| over the box).  The same seed gives the same
     field at every grid size whose Nyquist limit exceeds kmax.  The sum is evaluated as an
     inverse FFT of the mode amplitudes, on the CPU (numpy) or, with device set, on that torch
     device (returned as torch tensors there).  Returns drho (zero), u (3 fields)."""
     K, amp = random_fourier_modes(kmax, seed)
-    assert min(nx, ny, nz) > 2 * kmax, "grid too small for the requested modes"
+    # modes beyond a small grid's Nyquist limit alias exactly (e^{ikx} = e^{i(k mod n)x} on the
+    # grid points), which the accumulation into the spectrum reproduces
     if device is None:
         spec = np.zeros((3, nz, ny, nx), dtype=np.complex128)
         for (kx, ky, kz), a in zip(K, amp):
