@@ -598,7 +598,9 @@ int lbm_get_state(lbm_ctx* c, void* dst) {
     if (rc) return rc;
     if (!dst) return fail(c, LBM_ERR_ARG, "lbm_get_state: dst");
     const size_t row = (size_t)c->N * c->elem_bytes, pitch = (size_t)c->stride * c->elem_bytes;
-    cudaError_t e = cudaMemcpy2DAsync(dst, row, c->buf[c->cur], pitch, row, c->q, cudaMemcpyDefault, c->stream);
+    cudaError_t e = row == pitch  // contiguous populations: one linear copy
+                        ? cudaMemcpyAsync(dst, c->buf[c->cur], row * c->q, cudaMemcpyDefault, c->stream)
+                        : cudaMemcpy2DAsync(dst, row, c->buf[c->cur], pitch, row, c->q, cudaMemcpyDefault, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_state");
     return LBM_OK;
 }
@@ -608,7 +610,9 @@ int lbm_set_state(lbm_ctx* c, const void* src) {
     if (rc) return rc;
     if (!src) return fail(c, LBM_ERR_ARG, "lbm_set_state: src");
     const size_t row = (size_t)c->N * c->elem_bytes, pitch = (size_t)c->stride * c->elem_bytes;
-    cudaError_t e = cudaMemcpy2DAsync(c->buf[c->cur], pitch, src, row, row, c->q, cudaMemcpyDefault, c->stream);
+    cudaError_t e = row == pitch
+                        ? cudaMemcpyAsync(c->buf[c->cur], src, row * c->q, cudaMemcpyDefault, c->stream)
+                        : cudaMemcpy2DAsync(c->buf[c->cur], pitch, src, row, row, c->q, cudaMemcpyDefault, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_state");
     return LBM_OK;
 }
