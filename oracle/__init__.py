@@ -130,7 +130,7 @@ def force_bar(q, j, F, rho0=1.0):
 
 
 def n_strain(q):
-    return 6 if q == 19 else 3
+    return 3 if q == 9 else 6
 
 
 def strain_yu(q, mneq, s, rho0=1.0):
@@ -190,7 +190,7 @@ class Grid:
     def __init__(self, params, nx, ny, nz=1):
         self.p = params
         self.q = params.q
-        self.d = 3 if self.q == 19 else 2
+        self.d = 2 if self.q == 9 else 3
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
         self.shape = (nz, ny, nx)

@@ -24,10 +24,12 @@
  *            eq. (ChaiS)      Chai formula, S from the 19 non-equilibrium distributions
  *   Sec. 4.1 eq. (YuLuobasis) first-order non-equilibrium moments in terms of grad j
  *            (used to initialise a state whose strain rate is a given velocity gradient)
- *   Sec. 5.4 the Chai-based procedure for a Yu-type formula on another lattice (D2Q9 here)
+ *   Sec. 5.4 the Chai-based procedure for a Yu-type formula on another lattice (D2Q9, D3Q15)
  *
  * Readings where the paper is silent (each one is listed with its reason in the design notes):
  *   - D2Q9 lattice and moment basis: the Lallemand-Luo basis (paper names D2Q9 only).
+ *   - D3Q15 lattice and moment basis: the d'Humieres et al. (2002) 15-moment basis (paper
+ *     names D3Q15 only), equilibrium moments = T f_eq of the same He-Luo equilibrium.
  *   - Force: Guo-type discrete force Fbar_i = w_i[(c_i-u)/cs2 + (c_i.u)c_i/cs4].F, collision
  *     source (I - L/2) T Fbar, j = sum c f + F/2, and both strain formulas use the effective
  *     non-equilibrium (f - f_eq + Fbar/2).
@@ -101,6 +103,34 @@ static const int T9[9][9] = {{1, 1, 1, 1, 1, 1, 1, 1, 1},    {-4, -1, -1, -1, -1
                              {0, 0, -2, 0, 2, 1, 1, -1, -1},   {0, 1, -1, 1, -1, 0, 0, 0, 0},
                              {0, 0, 0, 0, 0, 1, -1, 1, -1}};
 
+/* D3Q15: the paper names this lattice but does not print it.  Velocity order: rest, +x, -x, +y,
+ * -y, +z, -z, then the eight corners (+-1, +-1, +-1) with c_x alternating fastest, then c_y,
+ * then c_z (first (1,1,1), last (-1,-1,-1)). */
+static const int C15[15][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                               {0, 0, 1},  {0, 0, -1},  {1, 1, 1},   {-1, 1, 1}, {1, -1, 1},
+                               {-1, -1, 1}, {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+
+/* D3Q15 moment matrix (d'Humieres et al. 2002 basis), rows are the polynomials
+ * 1, e = c^2 - 2, eps = (15c^4 - 55c^2 + 32)/2, j_x, q_x = (5c^2 - 13) c_x / 2, j_y, q_y, j_z, q_z,
+ * 3p_xx = 3c_x^2 - c^2, p_ww = c_y^2 - c_z^2, p_xy = c_x c_y, p_yz = c_y c_z, p_xz = c_x c_z,
+ * m_xyz = c_x c_y c_z, evaluated at C15. */
+static const int T15[15][15] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-2, -1, -1, -1, -1, -1, -1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {16, -4, -4, -4, -4, -4, -4, 1, 1, 1, 1, 1, 1, 1, 1},
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+    {0, -4, 4, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+    {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
+    {0, 0, 0, -4, 4, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 1, 1, 1, 1, -1, -1, -1, -1},
+    {0, 0, 0, 0, 0, -4, 4, 1, 1, 1, 1, -1, -1, -1, -1},
+    {0, 2, 2, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, -1, -1, 1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, -1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, -1, 1, 1, -1}};
+
 typedef struct {
     int q, d;
     int c[19][3];
@@ -112,7 +142,7 @@ typedef struct {
     int n_nu;
 } lattice_t;
 
-static lattice_t LAT19, LAT9;
+static lattice_t LAT19, LAT15, LAT9;
 static int lat_ready = 0;
 
 /* Gauss-Jordan inverse with partial pivoting, n <= 19.  Returns 0 on success. */
@@ -163,6 +193,17 @@ static void setup_lattice(lattice_t *L, int q) {
         int nu[5] = {9, 11, 13, 14, 15};
         for (int k = 0; k < 5; ++k) L->nu_idx[k] = nu[k];
         L->n_nu = 5;
+    } else if (q == 15) {
+        L->d = 3;
+        for (int i = 0; i < 15; ++i) {
+            for (int a = 0; a < 3; ++a) L->c[i][a] = C15[i][a];
+            for (int k = 0; k < 15; ++k) L->T[i][k] = T15[i][k];
+        }
+        /* 2/9 rest, 1/9 axis (i = 1..6), 1/72 corners (i = 7..14) */
+        for (int i = 0; i < 15; ++i) L->w[i] = (i == 0) ? 2.0 / 9.0 : (i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0);
+        /* s_nu relaxes the five viscous stresses 3p_xx, p_ww, p_xy, p_yz, p_xz (moments 9..13) */
+        for (int k = 0; k < 5; ++k) L->nu_idx[k] = 9 + k;
+        L->n_nu = 5;
     } else {
         L->d = 2;
         for (int i = 0; i < 9; ++i) {
@@ -184,10 +225,12 @@ static void setup_lattice(lattice_t *L, int q) {
 static const lattice_t *lattice(int q) {
     if (!lat_ready) {
         setup_lattice(&LAT19, 19);
+        setup_lattice(&LAT15, 15);
         setup_lattice(&LAT9, 9);
         lat_ready = 1;
     }
     if (q == 19) return &LAT19;
+    if (q == 15) return &LAT15;
     if (q == 9) return &LAT9;
     return NULL;
 }
@@ -234,7 +277,10 @@ int or_feq(int q, double drho, const double *j, double rho0, double *feq) {
  * lines in the printed set are read so that moment 9 = 3p_xx, 10 = 3pi_xx, 11 = p_ww and
  * 12 = pi_ww follow the moment vector eq. (moment) and the first row-block of eq. (solvem).
  * D2Q9 (Lallemand-Luo basis with the He-Luo equilibrium):
- *   (drho, -2 drho + 3 j^2/rho0, drho - 3 j^2/rho0, jx, -jx, jy, -jy, (jx^2 - jy^2)/rho0, jx jy/rho0). */
+ *   (drho, -2 drho + 3 j^2/rho0, drho - 3 j^2/rho0, jx, -jx, jy, -jy, (jx^2 - jy^2)/rho0, jx jy/rho0).
+ * D3Q15 (d'Humieres basis with the He-Luo equilibrium, i.e. T f_eq worked out by hand):
+ *   (drho, -drho + j^2/rho0, drho - 5 j^2/rho0, jx, -7jx/3, jy, -7jy/3, jz, -7jz/3,
+ *    (3jx^2 - j^2)/rho0, (jy^2 - jz^2)/rho0, jx jy/rho0, jy jz/rho0, jx jz/rho0, 0). */
 int or_meq(int q, double drho, const double *j, double rho0, double *meq) {
     if (q == 19) {
         const double w_eps = 3.0, w_epsj = -11.0 / 2.0, w_xx = -1.0 / 2.0;
@@ -259,6 +305,26 @@ int or_meq(int q, double drho, const double *j, double rho0, double *meq) {
         meq[16] = 0.0;
         meq[17] = 0.0;
         meq[18] = 0.0;
+        return OR_OK;
+    }
+    if (q == 15) {
+        double jx = j[0], jy = j[1], jz = j[2];
+        double jj = jx * jx + jy * jy + jz * jz;
+        meq[0] = drho;
+        meq[1] = -drho + jj / rho0;
+        meq[2] = drho - 5.0 * jj / rho0;
+        meq[3] = jx;
+        meq[4] = -7.0 * jx / 3.0;
+        meq[5] = jy;
+        meq[6] = -7.0 * jy / 3.0;
+        meq[7] = jz;
+        meq[8] = -7.0 * jz / 3.0;
+        meq[9] = (3.0 * jx * jx - jj) / rho0;
+        meq[10] = (jy * jy - jz * jz) / rho0;
+        meq[11] = jx * jy / rho0;
+        meq[12] = jy * jz / rho0;
+        meq[13] = jx * jz / rho0;
+        meq[14] = 0.0;
         return OR_OK;
     }
     if (q == 9) {
@@ -298,12 +364,17 @@ int or_force_bar(int q, const double *j, double rho0, const double *F, double *F
 }
 
 /* Number of strain-rate components stored: 6 in 3D (xx, yy, zz, xy, yz, xz), 3 in 2D (xx, yy, xy). */
-static int n_strain(int q) { return q == 19 ? 6 : 3; }
+static int n_strain(int q) { return q == 9 ? 3 : 6; }
 
 /* Yu formula, eq. (LuoS), written as printed (delta_t = 1, eps m^(1) = m - m_eq).
  * s holds all q rates; the formula reads s_1 and s_9 (it assumes s_9 = s_11 = s_13..15).
  * D2Q9: the Yu-type formula obtained by the Sec. 5.4 procedure from Chai's formula:
- *   S_xx,yy = -(s_e m_e +- 3 s_nu m_pxx) / (4 rho0),  S_xy = -3 s_nu m_pxy / (2 rho0). */
+ *   S_xx,yy = -(s_e m_e +- 3 s_nu m_pxx) / (4 rho0),  S_xy = -3 s_nu m_pxy / (2 rho0).
+ * D3Q15: the same procedure (S = -3/(2 rho0) sum_i c_i c_i [T^-1 L m_neq]_i with the d'Humieres
+ * basis) gives
+ *   S_xx = -(s_e m_e + s_nu m_3pxx) / (2 rho0),
+ *   S_yy,zz = -(2 s_e m_e - s_nu m_3pxx +- 3 s_nu m_pww) / (4 rho0),
+ *   S_xy = -3 s_nu m_pxy / (2 rho0),  S_yz = -3 s_nu m_pyz / (2 rho0),  S_xz = -3 s_nu m_pxz / (2 rho0). */
 int or_strain_yu(int q, const double *mneq, const double *s, double rho0, double *S) {
     if (q == 19) {
         double m1 = mneq[1], m9 = mneq[9], m11 = mneq[11];
@@ -314,6 +385,17 @@ int or_strain_yu(int q, const double *mneq, const double *s, double rho0, double
         S[3] = -3.0 * s9 * mneq[13] / (2.0 * rho0); /* xy */
         S[4] = -3.0 * s9 * mneq[14] / (2.0 * rho0); /* yz */
         S[5] = -3.0 * s9 * mneq[15] / (2.0 * rho0); /* zx */
+        return OR_OK;
+    }
+    if (q == 15) {
+        double se = s[1], snu = s[9];
+        double e = se * mneq[1], p = snu * mneq[9], w = snu * mneq[10];
+        S[0] = -(e + p) / (2.0 * rho0);
+        S[1] = -(2.0 * e - p + 3.0 * w) / (4.0 * rho0);
+        S[2] = -(2.0 * e - p - 3.0 * w) / (4.0 * rho0);
+        S[3] = -3.0 * snu * mneq[11] / (2.0 * rho0); /* xy */
+        S[4] = -3.0 * snu * mneq[12] / (2.0 * rho0); /* yz */
+        S[5] = -3.0 * snu * mneq[13] / (2.0 * rho0); /* zx */
         return OR_OK;
     }
     if (q == 9) {
@@ -349,8 +431,8 @@ int or_strain_chai(int q, const double *fneq, const double *s, double rho0, doub
     static const int ab2[3][2] = {{0, 0}, {1, 1}, {0, 1}};
     int ns = n_strain(q);
     for (int p = 0; p < ns; ++p) {
-        int a = (q == 19) ? ab3[p][0] : ab2[p][0];
-        int b = (q == 19) ? ab3[p][1] : ab2[p][1];
+        int a = (L->d == 3) ? ab3[p][0] : ab2[p][0];
+        int b = (L->d == 3) ? ab3[p][1] : ab2[p][1];
         double N = 0.0;
         for (int i = 0; i < q; ++i) N += L->c[i][a] * L->c[i][b] * M[i];
         S[p] = -N / (2.0 * rho0 * CS2);
@@ -363,7 +445,7 @@ int or_strain_chai(int q, const double *fneq, const double *s, double rho0, doub
 /* ------------------------------------------------------------------------------------------ */
 
 typedef struct {
-    int q;            /* 9 or 19 */
+    int q;            /* 9, 15 or 19 */
     int closure;      /* CL_NEWTON, CL_SMAG, CL_POWERLAW */
     int formula;      /* F_YU or F_CHAI: the route whose S feeds the closure */
     int smag_iters;   /* fixed number of fixed-point sweeps for Smagorinsky */
@@ -381,7 +463,7 @@ static int strain_components(int q) { return n_strain(q); }
 static double strain_norm(int q, const double *S) {
     /* |S| = sqrt(2 S:S) */
     double ss;
-    if (q == 19)
+    if (q != 9)
         ss = S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]);
     else
         ss = S[0] * S[0] + S[1] * S[1] + 2.0 * S[2] * S[2];
@@ -622,6 +704,10 @@ int or_step(const or_params *p, int nx, int ny, int nz, const double *fpost, con
  *   m15 = -(d_z j_x + d_x j_z)/(3 s_nu);
  * D2Q9 (same procedure with the D2Q9 Yu-type formula):
  *   m_e = -2 div j / s_e,  m_pxx = -2 (d_x j_x - d_y j_y)/(3 s_nu),  m_pxy = -(d_x j_y + d_y j_x)/(3 s_nu).
+ * D3Q15 (the first-order Chapman-Enskog moments -(1/s_k) T (d_t + c.grad) f_eq worked out for the
+ * d'Humieres basis):
+ *   m_e = -2 div j / (3 s_e),  m_3pxx = -2 (3 d_x j_x - div j)/(3 s_nu),  m_pww = -2 (d_y j_y - d_z j_z)/(3 s_nu),
+ *   m_pxy = -(d_x j_y + d_y j_x)/(3 s_nu),  m_pyz = -(d_y j_z + d_z j_y)/(3 s_nu),  m_pxz = -(d_x j_z + d_z j_x)/(3 s_nu).
  * s_nu is the closure's value for the given gradient (explicit, since S is given).
  * grad_u: d*d x N, entry (a*d + b) = d u_a / d x_b; NULL for a pure equilibrium.
  * The buffer written is the post-collision state of step -1: f(x,0) is un-streamed so that the
@@ -652,7 +738,7 @@ int or_init(const or_params *p, int nx, int ny, int nz, const double *drho, cons
                     double Sx[6];
                     double snu = p->s[L->nu_idx[0]];
                     if (p->closure != CL_NEWTON) {
-                        if (q == 19) {
+                        if (d == 3) {
                             Sx[0] = G[0][0] / p->rho0;
                             Sx[1] = G[1][1] / p->rho0;
                             Sx[2] = G[2][2] / p->rho0;
@@ -683,6 +769,13 @@ int or_init(const or_params *p, int nx, int ny, int nz, const double *drho, cons
                         mneq[13] = -(G[1][0] + G[0][1]) / (3.0 * snu);
                         mneq[14] = -(G[2][1] + G[1][2]) / (3.0 * snu);
                         mneq[15] = -(G[0][2] + G[2][0]) / (3.0 * snu);
+                    } else if (q == 15) {
+                        mneq[1] = -2.0 / (3.0 * p->s[1]) * divj;
+                        mneq[9] = -2.0 / (3.0 * snu) * (3.0 * G[0][0] - divj);
+                        mneq[10] = -2.0 / (3.0 * snu) * (G[1][1] - G[2][2]);
+                        mneq[11] = -(G[1][0] + G[0][1]) / (3.0 * snu);
+                        mneq[12] = -(G[2][1] + G[1][2]) / (3.0 * snu);
+                        mneq[13] = -(G[0][2] + G[2][0]) / (3.0 * snu);
                     } else {
                         mneq[1] = -2.0 * divj / p->s[1];
                         mneq[7] = -2.0 * (G[0][0] - G[1][1]) / (3.0 * snu);

@@ -8,21 +8,23 @@ from paper_1704_07559_gb300 import inputs as I
 
 TAU = 0.6
 S19 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / TAU, 1.4, 1 / TAU, 1.4, 1 / TAU, 1 / TAU, 1 / TAU, 1.98, 1.98, 1.98]
+S15 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / TAU, 1 / TAU, 1 / TAU, 1 / TAU, 1 / TAU, 1.98]
 S9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / TAU, 1 / TAU]
+VISCOUS = {19: (9, 11, 13, 14, 15), 15: (9, 10, 11, 12, 13), 9: (7, 8)}
 PER = [O.PERIODIC] * 6
 CHANNEL = [O.PERIODIC, O.PERIODIC, O.WALL, O.WALL, O.PERIODIC, O.PERIODIC]
 
 
 def rates(q, tau=TAU):
-    s = list(S19 if q == 19 else S9)
-    for k in ((9, 11, 13, 14, 15) if q == 19 else (7, 8)):
+    s = list({19: S19, 15: S15, 9: S9}[q])
+    for k in VISCOUS[q]:
         s[k] = 1.0 / tau
     return s
 
 
 def strain_from_grad(q, g):
     """Symmetric part of a velocity gradient in the oracle's component order."""
-    if q == 19:
+    if q != 9:
         return np.stack([g[0], g[4], g[8], 0.5 * (g[1] + g[3]), 0.5 * (g[5] + g[7]), 0.5 * (g[2] + g[6])])
     return np.stack([g[0], g[3], 0.5 * (g[1] + g[2])])
 
@@ -31,13 +33,13 @@ def strain_from_grad(q, g):
 # special cases that reduce to textbook routines
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_srt_special_case_is_bgk(q):
     """With every rate 1/tau, the MRT collision is the BGK collision (eq. (ChaiS_srt) context):
     f* = f - (f - f_eq)/tau + (1 - 1/(2 tau)) Fbar, and Chai's S is the LBGK formula
     S = -sum c c (f - f_eq + Fbar/2) / (2 rho0 cs2 tau)."""
     c, w, T, Ti, opp = O.tables(q)
-    d = 3 if q == 19 else 2
+    d = 2 if q == 9 else 3
     rng = np.random.default_rng(q)
     tau = 0.77
     p = O.make_params(q, [1.0 / tau] * q, formula=O.CHAI)
@@ -55,12 +57,12 @@ def test_srt_special_case_is_bgk(q):
         cc = c[:, :d].astype(float)
         P = np.einsum("i,ia,ib->ab", f - fe + 0.5 * Fb, cc, cc)
         Sl = -P / (2 * tau / 3)
-        want = [Sl[0, 0], Sl[1, 1], Sl[2, 2], Sl[0, 1], Sl[1, 2], Sl[0, 2]] if q == 19 else [Sl[0, 0], Sl[1, 1],
+        want = [Sl[0, 0], Sl[1, 1], Sl[2, 2], Sl[0, 1], Sl[1, 2], Sl[0, 2]] if q != 9 else [Sl[0, 0], Sl[1, 1],
                                                                                               Sl[0, 1]]
         assert np.abs(S - np.array(want)).max() < 1e-16
 
 
-@pytest.mark.parametrize("q,dims", [(19, (5, 4, 3)), (9, (7, 5, 1))])
+@pytest.mark.parametrize("q,dims", [(19, (5, 4, 3)), (15, (5, 4, 3)), (9, (7, 5, 1))])
 def test_zero_rates_is_pure_streaming(q, dims):
     """With all rates zero and no force the step is free streaming: f_i(x + c_i) = f_i(x), a
     periodic shift of each population array (numpy roll), up to the rounding of T^-1 T."""
@@ -90,11 +92,11 @@ def test_bounce_back_with_zero_rates_is_a_permutation():
 
 
 @pytest.mark.parametrize("q,formula,closure", [(19, O.YU, O.NEWTON), (19, O.CHAI, O.SMAG), (9, O.CHAI, O.POWERLAW),
-                                               (9, O.YU, O.NEWTON)])
+                                               (9, O.YU, O.NEWTON), (15, O.YU, O.SMAG), (15, O.CHAI, O.POWERLAW)])
 def test_conservation_periodic(q, formula, closure):
     """Mass and momentum are collision invariants (s_0 = s_3 = s_5 = s_7 = 0) and periodic
     streaming permutes populations: the global sums stay fixed to rounding."""
-    dims = (6, 5, 4) if q == 19 else (9, 7, 1)
+    dims = (6, 5, 4) if q != 9 else (9, 7, 1)
     p = O.make_params(q, rates(q), formula=formula, closure=closure, smag_cs=0.17, pl_n=0.6, pl_k=0.01)
     G = O.Grid(p, *dims)
     c, w, T, Ti, opp = O.tables(q)
@@ -106,12 +108,12 @@ def test_conservation_periodic(q, formula, closure):
     assert np.abs(s1 - s0).max() < 1e-13 * G.N * np.abs(f).max()
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_uniform_force_momentum_growth(q):
     """With a uniform body force F each step adds F to the momentum of every node:
     sum j grows by N F per step, mass is unchanged."""
-    d = 3 if q == 19 else 2
-    dims = (5, 4, 3) if q == 19 else (6, 5, 1)
+    d = 2 if q == 9 else 3
+    dims = (5, 4, 3) if q != 9 else (6, 5, 1)
     F = np.array([2e-5, -1e-5, 3e-5])[:d]
     p = O.make_params(q, rates(q))
     G = O.Grid(p, *dims)
@@ -124,14 +126,14 @@ def test_uniform_force_momentum_growth(q):
         assert np.abs(s[1:] - (s0[1:] + n * G.N * F)).max() < 1e-15 * G.N
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 @pytest.mark.parametrize("formula", [O.YU, O.CHAI])
 def test_uniform_flow_under_force_has_zero_strain(q, formula):
     """A spatially uniform flow accelerated by a uniform force has no velocity gradient, so the
     strain rate is zero at every step.  This fixes the half-force shift of both formulas:
     without it S would be of order u F (~1e-7 here)."""
-    d = 3 if q == 19 else 2
-    dims = (3, 2, 2) if q == 19 else (3, 2, 1)
+    d = 2 if q == 9 else 3
+    dims = (3, 2, 2) if q != 9 else (3, 2, 1)
     F = np.array([1e-5, -2e-5, 3e-5])[:d]
     p = O.make_params(q, rates(q), formula=formula)
     G = O.Grid(p, *dims)
@@ -147,11 +149,11 @@ def test_uniform_flow_under_force_has_zero_strain(q, formula):
     assert np.abs(out["u"][0] - (0.02 + 9 * F[0])).max() < 1e-15
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_bounce_back_conserves_mass(q):
     """Halfway bounce-back on every face returns each outgoing population to its node: mass is
     conserved to rounding (momentum is not, by design)."""
-    dims = (5, 6, 4) if q == 19 else (8, 6, 1)
+    dims = (5, 6, 4) if q != 9 else (8, 6, 1)
     p = O.make_params(q, rates(q), bc=[O.WALL] * 6, formula=O.CHAI)
     G = O.Grid(p, *dims)
     f = I.random_populations(q, G.shape, scale=2e-3, seed=5)
@@ -274,11 +276,11 @@ def test_power_law_fixed_point(n_index):
 # exact flows
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_initial_strain_equals_analytic(q):
     """Initialisation by the first-order non-equilibrium moments (eq. (YuLuobasis)) gives a state
     whose strain rate by either formula is the prescribed velocity gradient's symmetric part."""
-    if q == 19:
+    if q != 9:
         cases = [I.taylor_green_3d(8, u0=0.03), I.abc_flow(8, u0=0.03)]
         dims = (8, 8, 8)
     else:
@@ -296,11 +298,12 @@ def test_initial_strain_equals_analytic(q):
                 assert np.abs(r["u"] - u).max() < 1e-16
 
 
+@pytest.mark.parametrize("q", [19, 15])
 @pytest.mark.parametrize("plane,dims", [("xy", (16, 16, 2)), ("yz", (2, 16, 16)), ("xz", (16, 2, 16))])
-def test_taylor_green_decay_in_each_plane(plane, dims):
+def test_taylor_green_decay_in_each_plane(plane, dims, q):
     """The 2D Taylor-Green vortex is an exact Navier-Stokes solution whose strain rate decays as
     exp(-2 nu k^2 t), nu = (tau - 1/2)/3.  Run in each coordinate plane of the D3Q19 lattice
-    (exercising every strain component) both routes reproduce the analytic field to the
+    (exercising every strain component; D3Q19 and D3Q15) both routes reproduce the analytic field to the
     scheme's second-order accuracy (measured 1.3e-2 relative at n = 16 after 50 steps)."""
     n = 16
     drho, u, g = I.taylor_green_2d(*dims, u0=0.01, plane=plane)
@@ -308,9 +311,9 @@ def test_taylor_green_decay_in_each_plane(plane, dims):
     k = 2 * np.pi / n
     T = 50
     dec = np.exp(-2 * nu * k * k * T)
-    Sa = strain_from_grad(19, g) * dec
+    Sa = strain_from_grad(q, g) * dec
     for formula in (O.YU, O.CHAI):
-        p = O.make_params(19, rates(19), formula=formula)
+        p = O.make_params(q, rates(q), formula=formula)
         G = O.Grid(p, *dims)
         f = G.init(drho, u, g)
         f = G.run(f, T)
@@ -339,7 +342,7 @@ def test_abc_flow_decay():
     assert np.abs(S - Sa).max() / np.abs(Sa).max() < 3e-2
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_second_order_convergence(q):
     """Sec. 5.1: the strain rate is second-order accurate in space.  Diffusive scaling
     (u0 ~ 1/n, steps ~ n^2) of the 2D Taylor-Green vortex: the relative L2 error of S falls by
@@ -362,7 +365,7 @@ def test_second_order_convergence(q):
     assert slopes.min() >= 1.9, (errs, slopes)
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 @pytest.mark.parametrize("formula", [O.YU, O.CHAI])
 def test_poiseuille_channel(q, formula):
     """Force-driven channel between halfway bounce-back walls: in the steady state the shear
@@ -371,7 +374,7 @@ def test_poiseuille_channel(q, formula):
     tau = 0.8
     nu = (tau - 0.5) / 3
     H, g = 16, 1e-6
-    d = 3 if q == 19 else 2
+    d = 2 if q == 9 else 3
     F = np.zeros(d)
     F[0] = g
     p = O.make_params(q, rates(q, tau), bc=CHANNEL, formula=formula)
@@ -381,18 +384,18 @@ def test_poiseuille_channel(q, formula):
     S = G.readout(f, force=F)["S"][:, 0, :, 0]
     y = np.arange(H)
     Sxy = -(g / (2 * nu)) * (y - (H - 1) / 2)
-    ixy = 3 if q == 19 else 2
+    ixy = 2 if q == 9 else 3
     assert np.abs(S[ixy] - Sxy).max() < 1e-9 * np.abs(Sxy).max()
     assert np.abs(S[1]).max() < 1e-14 * np.abs(Sxy).max()
     assert np.abs(S[0]).max() < 2.0 * np.abs(Sxy).max() ** 2
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_couette_moving_lid(q):
     """Plane Couette flow between a wall at y = -1/2 and a lid moving at U at y = H - 1/2:
     steady u_x = U (y + 1/2)/H and uniform S_xy = U / (2H) (halfway bounce-back with the moving
     wall term is exact for a linear profile)."""
-    d = 3 if q == 19 else 2
+    d = 2 if q == 9 else 3
     H, U = 16, 0.01
     lid = [[0.0, 0.0, 0.0] for _ in range(6)]
     lid[3] = [U, 0.0, 0.0]
@@ -401,7 +404,7 @@ def test_couette_moving_lid(q):
     G = O.Grid(p, 1, H, 1)
     f = G.run(G.init(np.zeros((1, H, 1)), np.zeros((d, 1, H, 1))), 6000)
     r = G.readout(f)
-    ixy = 3 if q == 19 else 2
+    ixy = 2 if q == 9 else 3
     assert np.abs(r["S"][ixy] - U / (2 * H)).max() < 1e-9 * U / (2 * H)
     y = np.arange(H)
     assert np.abs(r["u"][0, 0, :, 0] - U * (y + 0.5) / H).max() < 1e-9 * U

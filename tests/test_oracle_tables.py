@@ -54,6 +54,34 @@ def test_d3q19_velocity_set_and_weights():
     assert (T[3] == c[:, 0]).all() and (T[5] == c[:, 1]).all() and (T[7] == c[:, 2]).all()
 
 
+def test_d3q15_velocity_set_and_weights():
+    """D3Q15 (named, not printed, by the paper): rest + 6 axis + 8 corner velocities with weights
+    2/9, 1/9, 1/72; the quadrature is isotropic to fourth order like D3Q19's."""
+    c, w, T, Ti, opp = O.tables(15)
+    c2 = (c * c).sum(1)
+    assert list(c2) == [0] + [1] * 6 + [3] * 8
+    assert all((c[opp[i]] == -c[i]).all() for i in range(15))
+    assert abs(w.sum() - 1) < 1e-15
+    d = np.eye(3)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), d / 3, atol=1e-15)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(m4, iso, atol=1e-15)
+    assert (T[3] == c[:, 0]).all() and (T[5] == c[:, 1]).all() and (T[7] == c[:, 2]).all()
+
+
+def test_d3q15_rows_are_the_basis_polynomials():
+    """Each row of the D3Q15 matrix is its defining polynomial of the velocity (d'Humieres et al.
+    2002 basis) evaluated on the velocity set."""
+    c, w, T, Ti, opp = O.tables(15)
+    x, y, z = (c[:, a].astype(float) for a in range(3))
+    c2 = x * x + y * y + z * z
+    rows = [np.ones(15), c2 - 2, (15 * c2 ** 2 - 55 * c2 + 32) / 2, x, (5 * c2 - 13) * x / 2, y,
+            (5 * c2 - 13) * y / 2, z, (5 * c2 - 13) * z / 2, 3 * x * x - c2, y * y - z * z, x * y, y * z, x * z,
+            x * y * z]
+    assert np.array_equal(T, np.array(rows))
+
+
 def test_d2q9_velocity_set_and_weights():
     c, w, T, Ti, opp = O.tables(9)
     assert abs(w.sum() - 1) < 1e-15
@@ -66,7 +94,7 @@ def test_d2q9_velocity_set_and_weights():
     assert (T[3] == c[:, 0]).all() and (T[5] == c[:, 1]).all()
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_moment_matrix_orthogonal_and_inverse(q):
     c, w, T, Ti, opp = O.tables(q)
     G = T @ T.T
@@ -76,6 +104,8 @@ def test_moment_matrix_orthogonal_and_inverse(q):
     assert np.abs(T @ Ti - np.eye(q)).max() < 1e-14
     if q == 19:
         assert list(np.diag(G)) == [19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4, 8, 8, 8]
+    elif q == 15:
+        assert list(np.diag(G)) == [15, 18, 360, 10, 40, 10, 40, 10, 40, 12, 4, 8, 8, 8, 8]
     else:
         assert list(np.diag(G)) == [9, 36, 36, 6, 12, 6, 12, 4, 4]
 
@@ -105,7 +135,7 @@ def rng_states(n, seed=0):
         yield rng.normal(scale=1e-2), rng.normal(scale=3e-2, size=3)
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_equilibrium_moments_closed_form(q):
     """eq. (meq) (closed-form m_eq) equals T f_eq of eq. (edf), at random states and rho0 != 1."""
     c, w, T, Ti, opp = O.tables(q)
@@ -119,12 +149,12 @@ def test_equilibrium_moments_closed_form(q):
             assert np.abs(T @ fe - me).max() < 1e-15
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_equilibrium_velocity_moments(q):
     """The He-Luo equilibrium satisfies eq. (cfeqmoment_) of Sec. 4.2:
     sum f = drho, sum c f = j, sum cc f = cs2 drho I + rho0 u u, sum ccc f = cs2 rho0 (delta u)."""
     c, w, T, Ti, opp = O.tables(q)
-    d = 3 if q == 19 else 2
+    d = 2 if q == 9 else 3
     cc = c[:, :d].astype(float)
     I = np.eye(d)
     for drho, j in rng_states(20, seed=7):
@@ -207,18 +237,33 @@ def test_yu_chai_differ_when_rates_split():
     assert yu_chai_pair(19, s, 1) > 1e-3
 
 
+def test_yu_type_equals_chai_d3q15():
+    """Sec. 5.4 procedure on D3Q15: the Yu-type formula derived from Chai's equals Chai's, for the
+    workload rates and for random rates with one viscous rate on moments 9..13."""
+    s = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2] + [1 / 0.6] * 5 + [1.98]
+    assert yu_chai_pair(15, s, 6) < 1e-13
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        s = list(rng.uniform(0.3, 1.95, size=15))
+        for k in (0, 3, 5, 7):
+            s[k] = 0.0
+        for k in (10, 11, 12, 13):
+            s[k] = s[9]
+        assert yu_chai_pair(15, s, 9, rho0=0.9) < 1e-13
+
+
 def test_yu_type_equals_chai_d2q9():
     """Sec. 5.4 procedure on D2Q9: the Yu-type formula derived from Chai's equals Chai's."""
     s = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / 0.7, 1 / 0.7]
     assert yu_chai_pair(9, s, 4) < 1e-13
 
 
-@pytest.mark.parametrize("q", [19, 9])
+@pytest.mark.parametrize("q", [19, 15, 9])
 def test_force_moments(q):
     """Guo-type discrete force: sum Fbar = 0, sum c Fbar = F, sum cc Fbar = uF + Fu, and T Fbar is
     the derivative of the closed-form m_eq along F (central difference of a quadratic)."""
     c, w, T, Ti, opp = O.tables(q)
-    d = 3 if q == 19 else 2
+    d = 2 if q == 9 else 3
     rng = np.random.default_rng(11)
     for _ in range(10):
         rho0 = 1.0 + 0.2 * rng.random()
@@ -237,3 +282,45 @@ def test_force_moments(q):
         h = 1.0
         dm = (O.meq(q, 0.3, j + h * F, rho0) - O.meq(q, 0.3, j - h * F, rho0)) / (2 * h)
         assert np.abs(T @ Fb - dm).max() < 1e-15
+
+
+VISCOUS_SET = {19: [1, 9, 11, 13, 14, 15], 15: [1, 9, 10, 11, 12, 13], 9: [1, 7, 8]}
+
+
+@pytest.mark.parametrize("q", [19, 15, 9])
+def test_first_order_moments_by_advection_matrices(q):
+    """Sec. 4.1 / 5.4: the first-order non-equilibrium moments that initialise a velocity
+    gradient are m1 = -L^-1 [sum_a C^_a d_a m_eq + d_t m_eq] with C^_a = T C_a T^-1, worked out here
+    numerically from the tables (d_t drho = -div j, j linear in x, drho uniform).  The oracle's
+    initialisation, typed in by hand per lattice (D3Q19: eq. (YuLuobasis)), must hold exactly these
+    values in the moments that carry the strain rate."""
+    c, w, T, Ti, opp = O.tables(q)
+    d = 2 if q == 9 else 3
+    rng = np.random.default_rng(20 + q)
+    s = rng.uniform(0.6, 1.9, size=q)
+    nu = VISCOUS_SET[q][1:]
+    s[nu] = s[nu[0]]
+    for _ in range(4):
+        Gm = np.zeros((3, 3))
+        Gm[:d, :d] = rng.normal(scale=1e-2, size=(d, d))  # G[a, b] = d u_a / d x_b, rho0 = 1
+        # d m_eq / d j . v at j = 0 (m_eq is quadratic in j: the central difference is exact)
+        def dmeq(v):
+            return (O.meq(q, 0.0, v) - O.meq(q, 0.0, -v)) / 2
+        dmeq_drho = O.meq(q, 1.0, np.zeros(3)) - O.meq(q, 0.0, np.zeros(3))
+        src = -np.trace(Gm) * dmeq_drho
+        for a in range(d):
+            Ca = T @ np.diag(c[:, a].astype(float)) @ Ti
+            src += Ca @ dmeq(Gm[:, a])
+        m1 = -src / s
+        # the oracle's initial state on a single periodic node (pointwise, so no streaming mixes it)
+        shape = (1, 1, 1)
+        p = O.make_params(q, list(s))
+        G = O.Grid(p, 1, 1, 1)
+        grad = np.zeros((d * d,) + shape)
+        for a in range(d):
+            for b in range(d):
+                grad[a * d + b] = Gm[a, b]
+        f = G.init(np.zeros(shape), np.zeros((d,) + shape), grad_u=grad).reshape(q)
+        mneq = T @ f - O.meq(q, f.sum(), c.T @ f)
+        for k in VISCOUS_SET[q]:
+            assert abs(mneq[k] - m1[k]) < 1e-15, (k, mneq[k], m1[k])
