@@ -8,7 +8,8 @@ node updates per second) and the fraction of the measured HBM bandwidth that the
 traffic (19 populations read + 19 written, 152 bytes per node update) represents.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|fp16s|bf16s|fp64] [--formula yu|chai] [--no-variants] [--quick]
+                  [--precision fp32|fp16s|bf16s|fp64] [--formula yu|chai] [--lattice 19|15]
+                  [--no-variants] [--quick]
 
 --precision / --formula pick the headline (default fp32 / yu); --quick skips the end-to-end
 run, the other variants and the CPU baseline (used for profiler captures).
@@ -36,6 +37,7 @@ NX, NY, NZ = 256, 128, 128
 TAU0, CS, G = 0.51, 0.17, 1e-6
 RATES = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / TAU0, 1.4, 1 / TAU0, 1.4, 1 / TAU0, 1 / TAU0, 1 / TAU0, 1.98,
          1.98, 1.98]
+RATES15 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / TAU0, 1 / TAU0, 1 / TAU0, 1 / TAU0, 1 / TAU0, 1.98]
 BC = ["periodic", "periodic", "wall", "wall", "periodic", "periodic"]
 BYTES_PER_LUP = {"fp32": 152, "fp64": 304, "fp16s": 76, "bf16s": 76}
 STORAGE_NOTE = {"fp32": "fp32 populations, fp32 arithmetic", "fp64": "fp64 populations, fp64 arithmetic",
@@ -138,12 +140,12 @@ class ClockSampler:
 # our arm
 
 
-def make_lattice(precision="fp32", formula="yu", dims=(NX, NY, NZ)):
+def make_lattice(precision="fp32", formula="yu", dims=(NX, NY, NZ), lattice=19):
     from paper_1704_07559_gb300 import inputs as I
     from paper_1704_07559_gb300 import lbm
 
-    lat = lbm.Lattice(lbm.D3Q19, *dims, rates=RATES, force=[G, 0.0, 0.0], precision=precision, closure="smag",
-                      smag_cs=CS, formula=formula, bc=BC)
+    lat = lbm.Lattice(lattice, *dims, rates=RATES if lattice == 19 else RATES15, force=[G, 0.0, 0.0],
+                      precision=precision, closure="smag", smag_cs=CS, formula=formula, bc=BC)
     drho, u = I.channel_profile(*dims, u_centre=0.1, noise=0.01, seed=2)
     lat.init(drho, u)
     return lat
@@ -239,8 +241,10 @@ def run_ours(args):
 
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    lat = make_lattice(args.precision, args.formula)
+    lat = make_lattice(args.precision, args.formula, lattice=args.lattice)
     N = lat.N
+    lname = "D3Q%d" % args.lattice
+    bytes_per_lup = BYTES_PER_LUP[args.precision] * args.lattice // 19
 
     # timed region: barrier + synchronize on both sides, max over ranks
     lat.step(args.warmup)
@@ -263,22 +267,22 @@ def run_ours(args):
     # kernel duration per launch for the roofline (events around each launch)
     per = time_steps(lat, min(args.steps, 500), 0, per_launch=True)
     k_ms = statistics.mean(per)
-    achieved = BYTES_PER_LUP[args.precision] * N / (k_ms * 1e-3) / 1e9
+    achieved = bytes_per_lup * N / (k_ms * 1e-3) / 1e9
 
-    kernel = "k_step<D3Q19,%s,SMAG,%s,force>" % (args.precision, args.formula.upper())
+    kernel = "k_step<%s,%s,SMAG,%s,force>" % (lname, args.precision, args.formula.upper())
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": [NX, NY, NZ], "formula": args.formula,
-                   "closure": "smagorinsky", "precision": STORAGE_NOTE[args.precision],
+        "config": {"workload": WORKLOAD.replace("D3Q19", lname), "lattice": lname, "grid": [NX, NY, NZ],
+                   "formula": args.formula, "closure": "smagorinsky", "precision": STORAGE_NOTE[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (two 319 MB population buffers per step)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4),
-                     "traffic": captured_traffic(kernel) if args.precision == "fp32" and args.formula == "yu" else None,
+                     "traffic": captured_traffic(kernel),
                      "peak_kind": peak_kind, "kernel": kernel,
-                     "bytes_per_lup": BYTES_PER_LUP[args.precision],
+                     "bytes_per_lup": bytes_per_lup,
                      "kernel_ms": round(k_ms, 5)},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
@@ -314,6 +318,13 @@ def variants(args, hbm):
         n = steps if precision != "fp64" else max(5, steps // 10)
         k_ms = statistics.mean(time_steps(lat, n, max(3, args.warmup // 10), per_launch=True))
         res["channel"]["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
+        lat.close()
+        torch.cuda.empty_cache()
+    # the same channel on D3Q15 (d'Humieres basis; Yu-type formula of the Sec. 5.4 procedure)
+    for formula in ("yu", "chai"):
+        lat = make_lattice("fp32", formula, lattice=15)
+        k_ms = statistics.mean(time_steps(lat, steps, max(3, args.warmup // 10), per_launch=True))
+        res["channel"]["d3q15_fp32_%s" % formula] = rate(lat.N, k_ms, 2 * 15 * 4, hbm)
         lat.close()
         torch.cuda.empty_cache()
     for name, fn in (("box512", box512), ("precision64", precision64), ("cavity4096", cavity4096),
@@ -392,29 +403,54 @@ def precision64(args, hbm):
     return out
 
 
+CAVITY_U, CAVITY_RE = 0.05, 1000.0
+
+
+def cavity_lattice(Lc, nidx, formula):
+    """D2Q9 power-law lid-driven cavity of side Lc, lid velocity 0.05 on the +y face, consistency
+    K = U^(2-n) L^n / Re with Re = 1000, fluid at rest at t = 0, FP32 populations."""
+    import torch
+    from paper_1704_07559_gb300 import lbm
+
+    U = CAVITY_U
+    tau_ref = 0.5 + 3 * U * Lc / CAVITY_RE
+    r9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / tau_ref, 1 / tau_ref]
+    K = U ** (2 - nidx) * Lc ** nidx / CAVITY_RE
+    lat = lbm.Lattice(lbm.D2Q9, Lc, Lc, 1, rates=r9, precision="fp32", closure="powerlaw", formula=formula,
+                      pl_n=nidx, pl_k=K, pl_tau_min=0.505, pl_tau_max=5.0, bc=["wall", "wall", "wall", "lid"],
+                      lid_u={3: (U, 0.0, 0.0)})
+    lat.init(torch.zeros((1, Lc, Lc), dtype=torch.float64, device="cuda"),
+             torch.zeros((2, 1, Lc, Lc), dtype=torch.float64, device="cuda"))
+    return lat
+
+
 def cavity4096(args, hbm):
     """D2Q9 power-law lid-driven cavity, 4096^2, lid velocity 0.05, n in {0.5, 1, 1.5}, consistency
     K = U^(2-n) L^n / Re with Re = 1000, tau solved per node by fixed point, fluid at rest at t = 0."""
-    from paper_1704_07559_gb300 import lbm
-
     out = {}
-    Lc, U, Re = 4096, 0.05, 1000.0
-    tau_ref = 0.5 + 3 * U * Lc / Re
-    r9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / tau_ref, 1 / tau_ref]
     for nidx in (0.5, 1.0, 1.5):
-        K = U ** (2 - nidx) * Lc ** nidx / Re
         for formula in ("chai", "yu"):
-            lat = lbm.Lattice(lbm.D2Q9, Lc, Lc, 1, rates=r9, precision="fp32", closure="powerlaw", formula=formula,
-                              pl_n=nidx, pl_k=K, pl_tau_min=0.505, pl_tau_max=5.0, bc=["wall", "wall", "wall", "lid"],
-                              lid_u={3: (U, 0.0, 0.0)})
-            import torch
-
-            lat.init(torch.zeros((1, Lc, Lc), dtype=torch.float64, device="cuda"),
-                     torch.zeros((2, 1, Lc, Lc), dtype=torch.float64, device="cuda"))
+            lat = cavity_lattice(4096, nidx, formula)
             k_ms = statistics.mean(time_steps(lat, 50, 20, per_launch=True))
             out["n%.1f_%s" % (nidx, formula)] = rate(lat.N, k_ms, 72, hbm)
             lat.close()
     return out
+
+
+ADJ_N, ADJ_T, ADJ_SEG = 128, 256, 16
+
+
+def adjoint_lattice(precision="fp32", g=None):
+    """Adjoint workload lattice: 128^3 periodic Smagorinsky box bound to the force field g
+    (default N(0, (1e-5)^2), seed 5), started from the random Fourier field |k| <= 4, rms 0.01
+    (seed 6)."""
+    import torch
+    from paper_1704_07559_gb300 import inputs as I
+
+    n = ADJ_N
+    if g is None:
+        g = torch.from_numpy(I.gaussian_force(3, (n, n, n), std=1e-5, seed=5))
+    return box_lattice(n, precision, "yu", 4, 0.01, 6, with_force=g)
 
 
 def adjoint128(args, hbm):
@@ -424,11 +460,9 @@ def adjoint128(args, hbm):
     time of lbm_adjoint (forward with checkpoints + functional + reverse sweep with recompute),
     and their ratio."""
     import torch
-    from paper_1704_07559_gb300 import inputs as I
 
-    n, T, seg = 128, 256, 16
-    g = torch.from_numpy(I.gaussian_force(3, (n, n, n), std=1e-5, seed=5))
-    lat = box_lattice(n, "fp32", "yu", 4, 0.01, 6, with_force=g)
+    T, seg = ADJ_T, ADJ_SEG
+    lat = adjoint_lattice("fp32")
     f0 = lat.get_state().clone()
     lat.step(5)
     torch.cuda.synchronize()
@@ -458,20 +492,34 @@ def adjoint128(args, hbm):
             "reverse_over_forward": round((a_ms - f_ms) / f_ms, 3), "total_over_forward": round(a_ms / f_ms, 3)}
 
 
+TGV_N, TGV_U0, TGV_TAU, TGV_STEPS = 32, 0.02, 0.6, 500
+
+
+def tgv_rates():
+    r = list(RATES)
+    for k in (9, 11, 13, 14, 15):
+        r[k] = 1 / TGV_TAU
+    return r
+
+
+def tgv_lattice(formula="yu"):
+    """D3Q19 FP64 32^3 periodic Taylor-Green vortex, u0 = 0.02, tau = 0.6, Newtonian."""
+    from paper_1704_07559_gb300 import inputs as I
+    from paper_1704_07559_gb300 import lbm
+
+    lat = lbm.Lattice(lbm.D3Q19, TGV_N, TGV_N, TGV_N, rates=tgv_rates(), precision="fp64", closure="newton",
+                      formula=formula)
+    drho, u, g = I.taylor_green_3d(TGV_N, u0=TGV_U0)
+    lat.init(drho, u, g)
+    return lat
+
+
 def tgv32(args, hbm):
     """Correctness workload: D3Q19 FP64, 32^3 periodic Taylor-Green vortex u0 = 0.02, tau = 0.6,
     500 steps; S by Yu and by Chai, their difference, and the decay of S against the linear
     (Stokes) rate exp(-3 nu k^2 t) of this non-exact flow."""
-    from paper_1704_07559_gb300 import inputs as I
-    from paper_1704_07559_gb300 import lbm
-
-    n, u0, tau, T = 32, 0.02, 0.6, 500
-    r = list(RATES)
-    for k in (9, 11, 13, 14, 15):
-        r[k] = 1 / tau
-    lat = lbm.Lattice(lbm.D3Q19, n, n, n, rates=r, precision="fp64", closure="newton")
-    drho, u, g = I.taylor_green_3d(n, u0=u0)
-    lat.init(drho, u, g)
+    n, tau, T = TGV_N, TGV_TAU, TGV_STEPS
+    lat = tgv_lattice()
     S0 = lat.strain_rate("yu").abs().max().item()
     k_ms = statistics.mean(time_steps(lat, T, 0, per_launch=True))
     Sy, Sc = lat.strain_rate("yu"), lat.strain_rate("chai")
@@ -540,6 +588,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16s", "bf16s", "fp64"])
     ap.add_argument("--formula", default="yu", choices=["yu", "chai"])
+    ap.add_argument("--lattice", type=int, default=19, choices=[19, 15],
+                    help="19: the D3Q19 channel (default); 15: the same channel on D3Q15 (fp32/fp64 only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()

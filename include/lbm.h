@@ -2,13 +2,15 @@
  * lbm.h -- C ABI of the GB300 MRT lattice Boltzmann library (liblbm.so).
  *
  * The library runs the fused multiple-relaxation-time (MRT) lattice Boltzmann time step of the
- * He-Luo D3Q19 model (and its D2Q9 counterpart) on one NVIDIA GPU, forming the strain-rate
+ * He-Luo D3Q19 model (and its D2Q9 and D3Q15 counterparts) on one NVIDIA GPU, forming the strain-rate
  * tensor S at every node by either of the two routes compared by Zhang, Huang, Wang and Shi,
  * "The computation of strain rate tensor in multiple-relaxation-time lattice Boltzmann model"
  * (arXiv:1704.07559):
  *   LBM_YU    Yu's formula, eq. (LuoS): S from six non-equilibrium moments;
- *   LBM_CHAI  Chai's formula, eq. (ChaiS): S from the nineteen non-equilibrium distributions,
+ *   LBM_CHAI  Chai's formula, eq. (ChaiS): S from the q non-equilibrium distributions,
  *             -sum_i c_i c_i (T^-1 L T f_neq)_i / (2 rho0 cs^2).
+ * On D2Q9 and D3Q15, LBM_YU selects the Yu-type formula that the procedure of Sec. 5.4 derives
+ * from Chai's formula for that lattice's moment basis.
  * S feeds a strain-rate-dependent relaxation time (Smagorinsky eddy viscosity or a power-law
  * fluid) inside the same step.
  *
@@ -52,6 +54,7 @@ extern "C" {
 
 /* lattices (the value is q) */
 #define LBM_D2Q9 9
+#define LBM_D3Q15 15 /* d'Humieres 15-moment basis (the paper names the lattice, prints no table) */
 #define LBM_D3Q19 19
 
 /* population storage precision */
@@ -102,11 +105,13 @@ typedef struct lbm_ctx lbm_ctx;
 void lbm_default_params(lbm_params* p);
 
 /* Create a context for an nx x ny x nz lattice (nz = 1 for D2Q9).
- *  lattice  LBM_D2Q9 or LBM_D3Q19.
+ *  lattice  LBM_D2Q9, LBM_D3Q15 or LBM_D3Q19 (D3Q15: FP64 and FP32 storage only).
  *  rates    q relaxation rates s_0..s_{q-1} of the diagonal collision matrix, eq. (sD3Q15):
- *           the conserved entries (0, 3, 5, 7 in D3Q19; 0, 3, 5 in D2Q9) must be 0, every other
- *           entry lies in (0, 2).  The viscous entries (9, 11, 13, 14, 15 in D3Q19; 7, 8 in D2Q9)
- *           hold 1/tau0; they must be equal for the Yu route and for any closure.
+ *           the conserved entries (0, 3, 5, 7 in D3Q19 and D3Q15; 0, 3, 5 in D2Q9) must be 0,
+ *           every other entry lies in (0, 2).  The viscous entries (9, 11, 13, 14, 15 in D3Q19;
+ *           9..13 in D3Q15; 7, 8 in D2Q9) hold 1/tau0; they must be equal for the Yu route and
+ *           for any closure.  On D2Q9 and D3Q15 the Yu route is the Yu-type formula that the
+ *           Sec. 5.4 procedure derives from Chai's formula for that basis.
  *  force    d components of a uniform body-force density (rho0 g), or NULL for none.
  *  p        parameters, or NULL for the defaults.
  * Host pointers, read during the call only.  Errors: LBM_ERR_ARG for any violated rule above,
@@ -172,7 +177,8 @@ int lbm_set_state(lbm_ctx* ctx, const void* src);
  * caching pool) or a time-stepping loop with a latency budget (cudaMalloc / cudaFree may
  * synchronise the device and take unbounded time).  No context is used and nothing is allocated:
  * no cudaMalloc, cudaFree or allocating library routine is called.
- *  lattice, nx, ny, nz  as for lbm_create;  p: precision, bc, lid_u and rho0 are read;
+ *  lattice, nx, ny, nz  as for lbm_create (16-bit storage: D3Q19 only);  p: precision, bc,
+ *           lid_u and rho0 are read;
  *  force    d components of the uniform force density, or NULL;
  *  f        device pointer to one population buffer (q arrays of `stride` elements of the
  *           storage type, stride >= nx*ny*nz), holding post-collision populations as after

@@ -56,12 +56,27 @@ int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
 bool is_finite(double v) { return std::isfinite(v); }
 
 bool is_viscous(int q, int k) {
-    return q == 19 ? (k == 9 || k == 11 || k == 13 || k == 14 || k == 15) : (k == 7 || k == 8);
+    switch (q) {
+        case 19: return lbm::D3Q19::viscous(k);
+        case 15: return lbm::D3Q15::viscous(k);
+        default: return lbm::D2Q9::viscous(k);
+    }
 }
 bool is_conserved(int q, int k) {
-    return q == 19 ? (k == 0 || k == 3 || k == 5 || k == 7) : (k == 0 || k == 3 || k == 5);
+    switch (q) {
+        case 19: return lbm::D3Q19::conserved(k);
+        case 15: return lbm::D3Q15::conserved(k);
+        default: return lbm::D2Q9::conserved(k);
+    }
 }
-int first_viscous(int q) { return q == 19 ? 9 : 7; }
+int first_viscous(int q) { return q == 9 ? lbm::D2Q9::NU0 : lbm::D3Q19::NU0; }
+int row_norm2(int q, int k) {
+    switch (q) {
+        case 19: return lbm::norm2<lbm::D3Q19>(k);
+        case 15: return lbm::norm2<lbm::D3Q15>(k);
+        default: return lbm::norm2<lbm::D2Q9>(k);
+    }
+}
 
 bool viscous_rates_equal(const lbm_ctx* c) {
     const double s = c->rates[first_viscous(c->q)];
@@ -79,7 +94,7 @@ void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
     a->stride = c->stride;
     for (int k = 0; k < 19; ++k) {
         a->s[k] = R(k < c->q ? c->rates[k] : 0.0);
-        const int n2 = k >= c->q ? 1 : (c->q == 19 ? lbm::norm2<lbm::D3Q19>(k) : lbm::norm2<lbm::D2Q9>(k));
+        const int n2 = k >= c->q ? 1 : row_norm2(c->q, k);
         a->skn[k] = R(k < c->q ? c->rates[k] / n2 : 0.0);
     }
     for (int d = 0; d < 3; ++d) a->F[d] = R(c->force[d]);
@@ -122,7 +137,7 @@ bool has_force(const lbm_ctx* c) {
     return c->p.force_field || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
 }
 
-enum Tag { T_D3Q19_F64, T_D3Q19_F32, T_D3Q19_F16, T_D3Q19_BF16, T_D2Q9_F64, T_D2Q9_F32, T_NONE };
+enum Tag { T_D3Q19_F64, T_D3Q19_F32, T_D3Q19_F16, T_D3Q19_BF16, T_D3Q15_F64, T_D3Q15_F32, T_D2Q9_F64, T_D2Q9_F32, T_NONE };
 
 Tag tag_of(int q, int precision) {
     if (q == 19) {
@@ -131,6 +146,11 @@ Tag tag_of(int q, int precision) {
             case LBM_FP32: return T_D3Q19_F32;
             case LBM_FP16S: return T_D3Q19_F16;
             case LBM_BF16S: return T_D3Q19_BF16;
+        }
+    } else if (q == 15) {
+        switch (precision) {
+            case LBM_FP64: return T_D3Q15_F64;
+            case LBM_FP32: return T_D3Q15_F32;
         }
     } else if (q == 9) {
         switch (precision) {
@@ -155,8 +175,12 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
         a.tau_out = static_cast<double*>(tau);
         a.drho_out = static_cast<double*>(drho);
         a.u_out = static_cast<double*>(u);
-        return t == T_D3Q19_F64 ? lbm::step_d3q19_f64(a, c->p.closure, formula, force, c->stream)
-                                : lbm::step_d2q9_f64(a, c->p.closure, formula, force, c->stream);
+        switch (t) {
+            case T_D3Q19_F64: return lbm::step_d3q19_f64(a, c->p.closure, formula, force, c->stream);
+            case T_D3Q15_F64: return lbm::step_d3q15_f64(a, c->p.closure, formula, force, c->stream);
+            case T_D2Q9_F64: return lbm::step_d2q9_f64(a, c->p.closure, formula, force, c->stream);
+            default: return cudaErrorInvalidValue;
+        }
     }
     lbm::StepArgs<float> a;
     fill_args(c, &a);
@@ -170,6 +194,7 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
         case T_D3Q19_F32: return lbm::step_d3q19_f32(a, c->p.closure, formula, force, c->stream);
         case T_D3Q19_F16: return lbm::step_d3q19_f16(a, c->p.closure, formula, force, c->stream);
         case T_D3Q19_BF16: return lbm::step_d3q19_bf16(a, c->p.closure, formula, force, c->stream);
+        case T_D3Q15_F32: return lbm::step_d3q15_f32(a, c->p.closure, formula, force, c->stream);
         case T_D2Q9_F32: return lbm::step_d2q9_f32(a, c->p.closure, formula, force, c->stream);
         default: return cudaErrorInvalidValue;
     }
@@ -381,10 +406,10 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
         return LBM_ERR_ARG;
     };
     create_err[0] = '\0';
-    if (lattice != LBM_D3Q19 && lattice != LBM_D2Q9) return bad("lattice");
+    if (lattice != LBM_D3Q19 && lattice != LBM_D3Q15 && lattice != LBM_D2Q9) return bad("lattice");
     c->q = lattice;
-    c->d = lattice == LBM_D3Q19 ? 3 : 2;
-    c->ns = lattice == LBM_D3Q19 ? 6 : 3;
+    c->d = lattice == LBM_D2Q9 ? 2 : 3;
+    c->ns = lattice == LBM_D2Q9 ? 3 : 6;
     if (nx < 1 || ny < 1 || nz < 1) return bad("dims");
     if (c->d == 2 && nz != 1) return bad("nz");
     if (ny > 65535 || nz > 65535) return bad("ny/nz");
@@ -505,6 +530,12 @@ int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad
         case T_D3Q19_F64:
             e = lbm::init_d3q19_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
             break;
+        case T_D3Q15_F64:
+            e = lbm::init_d3q15_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
+            break;
+        case T_D3Q15_F32:
+            e = lbm::init_d3q15_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            break;
         case T_D2Q9_F64:
             e = lbm::init_d2q9_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
             break;
@@ -569,8 +600,12 @@ int lbm_sums(lbm_ctx* c, double* out) {
         lbm::StepArgs<double> a;
         fill_args(c, &a);
         set_buffers(c, &a, c->buf[c->cur], nullptr);
-        e = t == T_D3Q19_F64 ? lbm::sums_d3q19_f64(a, c->partial, c->result, c->stream)
-                             : lbm::sums_d2q9_f64(a, c->partial, c->result, c->stream);
+        switch (t) {
+            case T_D3Q19_F64: e = lbm::sums_d3q19_f64(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_F64: e = lbm::sums_d3q15_f64(a, c->partial, c->result, c->stream); break;
+            case T_D2Q9_F64: e = lbm::sums_d2q9_f64(a, c->partial, c->result, c->stream); break;
+            default: e = cudaErrorInvalidValue;
+        }
     } else {
         lbm::StepArgs<float> a;
         fill_args(c, &a);
@@ -579,6 +614,7 @@ int lbm_sums(lbm_ctx* c, double* out) {
             case T_D3Q19_F32: e = lbm::sums_d3q19_f32(a, c->partial, c->result, c->stream); break;
             case T_D3Q19_F16: e = lbm::sums_d3q19_f16(a, c->partial, c->result, c->stream); break;
             case T_D3Q19_BF16: e = lbm::sums_d3q19_bf16(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_F32: e = lbm::sums_d3q15_f32(a, c->partial, c->result, c->stream); break;
             case T_D2Q9_F32: e = lbm::sums_d2q9_f32(a, c->partial, c->result, c->stream); break;
             default: e = cudaErrorInvalidValue;
         }

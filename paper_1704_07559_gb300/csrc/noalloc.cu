@@ -69,7 +69,7 @@ void fill(lbm::StepArgs<R>* a, int q, int nx, int ny, int nz, const lbm_params* 
     a->stride = stride;
     a->src = f;
     for (int i = 0; i < q; ++i) a->srcp[i] = static_cast<const char*>(f) + (size_t)i * stride * elem;
-    const int d = q == 19 ? 3 : 2;
+    const int d = q == LBM_D2Q9 ? 2 : 3;
     for (int k = 0; k < 3; ++k) a->F[k] = R((force && k < d) ? force[k] : 0.0);
     a->rho0 = R(p->rho0);
     a->inv_rho0 = R(1.0 / p->rho0);
@@ -89,8 +89,8 @@ void fill(lbm::StepArgs<R>* a, int q, int nx, int ny, int nz, const lbm_params* 
 extern "C" int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_params* p, const double* force,
                                 const void* f, int64_t stride, const void* force_field, double* out, void* stream) {
     // argument checks first: a rejected call touches no CUDA state
-    if ((lattice != LBM_D3Q19 && lattice != LBM_D2Q9) || !p || !f || !out) return LBM_ERR_ARG;
-    const int d = lattice == LBM_D3Q19 ? 3 : 2;
+    if ((lattice != LBM_D3Q19 && lattice != LBM_D3Q15 && lattice != LBM_D2Q9) || !p || !f || !out) return LBM_ERR_ARG;
+    const int d = lattice == LBM_D2Q9 ? 2 : 3;
     if (nx < 1 || ny < 1 || nz < 1 || (d == 2 && nz != 1) || ny > 65535 || nz > 65535) return LBM_ERR_ARG;
     const long long N = (long long)nx * ny * nz;
     if (N >= (1LL << 31) || stride < N) return LBM_ERR_ARG;
@@ -111,7 +111,7 @@ extern "C" int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_p
         case LBM_BF16S: elem = 2; break;
         default: return LBM_ERR_ARG;
     }
-    if (lattice == LBM_D2Q9 && elem == 2) return LBM_ERR_ARG;
+    if (lattice != LBM_D3Q19 && elem == 2) return LBM_ERR_ARG;
 
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return LBM_ERR_CUDA;
@@ -121,12 +121,16 @@ extern "C" int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_p
     if (p->precision == LBM_FP64) {
         lbm::StepArgs<double> a;
         fill(&a, lattice, nx, ny, nz, p, force, f, stride, elem, force_field);
-        e = lattice == LBM_D3Q19 ? run<lbm::D3Q19, double>(a, nb, scratch, s) : run<lbm::D2Q9, double>(a, nb, scratch, s);
+        e = lattice == LBM_D3Q19   ? run<lbm::D3Q19, double>(a, nb, scratch, s)
+            : lattice == LBM_D3Q15 ? run<lbm::D3Q15, double>(a, nb, scratch, s)
+                                   : run<lbm::D2Q9, double>(a, nb, scratch, s);
     } else {
         lbm::StepArgs<float> a;
         fill(&a, lattice, nx, ny, nz, p, force, f, stride, elem, force_field);
         if (lattice == LBM_D2Q9)
             e = run<lbm::D2Q9, float>(a, nb, scratch, s);
+        else if (lattice == LBM_D3Q15)
+            e = run<lbm::D3Q15, float>(a, nb, scratch, s);
         else if (p->precision == LBM_FP32)
             e = run<lbm::D3Q19, float>(a, nb, scratch, s);
         else if (p->precision == LBM_FP16S)

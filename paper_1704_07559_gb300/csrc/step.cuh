@@ -467,6 +467,73 @@ struct Eq<D3Q19> {
 };
 
 template <>
+struct Eq<D3Q15> {
+    // T f_eq of the He-Luo equilibrium on the d'Humieres D3Q15 basis
+    template <class R>
+    static __device__ __forceinline__ void meq(R drho, const R (&j)[3], const R (&u)[3], R (&m)[15]) {
+        const R ju = fma(j[0], u[0], fma(j[1], u[1], j[2] * u[2]));
+        m[0] = drho;
+        m[1] = ju - drho;
+        m[2] = fma(R(-5.0f), ju, drho);
+        m[3] = j[0];
+        m[4] = cst<R>(-7.0 / 3.0) * j[0];
+        m[5] = j[1];
+        m[6] = cst<R>(-7.0 / 3.0) * j[1];
+        m[7] = j[2];
+        m[8] = cst<R>(-7.0 / 3.0) * j[2];
+        m[9] = fma(R(3.0f) * j[0], u[0], -ju);
+        m[10] = fma(j[1], u[1], -(j[2] * u[2]));
+        m[11] = j[0] * u[1];
+        m[12] = j[1] * u[2];
+        m[13] = j[0] * u[2];
+        m[14] = R(0.0f);
+    }
+    template <class R>
+    static __device__ __forceinline__ void tforce(const R (&u)[3], const R (&F)[3], R (&t)[15]) {
+        const R uF = fma(u[0], F[0], fma(u[1], F[1], u[2] * F[2]));
+        t[0] = R(0.0f);
+        t[1] = R(2.0f) * uF;
+        t[2] = R(-10.0f) * uF;
+        t[3] = F[0];
+        t[4] = cst<R>(-7.0 / 3.0) * F[0];
+        t[5] = F[1];
+        t[6] = cst<R>(-7.0 / 3.0) * F[1];
+        t[7] = F[2];
+        t[8] = cst<R>(-7.0 / 3.0) * F[2];
+        t[9] = fma(R(6.0f) * u[0], F[0], R(-2.0f) * uF);
+        t[10] = R(2.0f) * fma(u[1], F[1], -(u[2] * F[2]));
+        t[11] = fma(u[0], F[1], u[1] * F[0]);
+        t[12] = fma(u[1], F[2], u[2] * F[1]);
+        t[13] = fma(u[0], F[2], u[2] * F[0]);
+        t[14] = R(0.0f);
+    }
+    // m_xyz has zero equilibrium and force parts
+    static __host__ __device__ constexpr bool ghost(int k) { return k == 14; }
+    // Yu-type D3Q15 formula (Sec. 5.4 procedure): S_xx = -(s_e m_e + s_nu m_3pxx)/(2 rho0),
+    // S_yy,zz = -(2 s_e m_e - s_nu m_3pxx +- 3 s_nu m_pww)/(4 rho0), S_ab = -3 s_nu m_pab/(2 rho0);
+    // c1 = s_e/(2 rho0)
+    template <class R>
+    static __device__ __forceinline__ void yu_split(const R (&mn)[15], R c1, R ir0, R (&A)[6], R (&B)[6]) {
+        const R a = -(c1 * mn[1]);
+        A[0] = a;
+        A[1] = a;
+        A[2] = a;
+        A[3] = R(0.0f);
+        A[4] = R(0.0f);
+        A[5] = R(0.0f);
+        const R h = R(0.25f) * ir0;
+        const R k = R(-1.5f) * ir0;
+        B[0] = (R(-0.5f) * ir0) * mn[9];
+        B[1] = h * fma(R(-3.0f), mn[10], mn[9]);
+        B[2] = h * fma(R(3.0f), mn[10], mn[9]);
+        B[3] = k * mn[11];
+        B[4] = k * mn[12];
+        B[5] = k * mn[13];
+    }
+    static constexpr double YU_A = 1.0 / 2.0;
+};
+
+template <>
 struct Eq<D2Q9> {
     template <class R>
     static __device__ __forceinline__ void meq(R drho, const R (&j)[3], const R (&u)[3], R (&m)[9]) {
@@ -521,7 +588,7 @@ __device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const
                                                   R (&DF)[L::NP]) {
     const R ju = fma(j[0], u[0], fma(j[1], u[1], j[2] * u[2]));
     const R base = fma(R(-1.5f), ju, drho);
-    constexpr double w0 = L::w36(0) / 36.0;
+    constexpr double w0 = double(L::wnum(0)) / L::WDEN;
     fe0 = cst<R>(w0) * base;
     R uF = R(0.0f);
     if constexpr (FORCE) {
@@ -533,7 +600,7 @@ __device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const
     sfor<L::NP>([&](auto p) {
         constexpr int i = L::pa(CV(p));
         constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-        constexpr double w = L::w36(i) / 36.0;
+        constexpr double w = double(L::wnum(i)) / L::WDEN;
         const R cj = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), j[0]), j[1]), j[2]);
         const R cu = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), u[0]), u[1]), u[2]);
         Pe[p] = cst<R>(2.0 * w) * fma(R(4.5f) * cj, cu, base);
@@ -670,7 +737,7 @@ __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y
             if (nout == 1 && ((a.lid_mask >> face) & 1)) {
                 const RS cu = RS(L::c(CV(i), 0)) * a.lid[face][0] + RS(L::c(CV(i), 1)) * a.lid[face][1] +
                               RS(L::c(CV(i), 2)) * a.lid[face][2];
-                v += RS(L::w36(CV(i)) / 6.0) * a.rho0 * cu;  // 2 w_i rho0 (c.u)/cs^2 = 6 w_i rho0 c.u
+                v += RS(double(6 * L::wnum(CV(i))) / L::WDEN) * a.rho0 * cu;  // 2 w_i rho0 (c.u)/cs^2 = 6 w_i rho0 c.u
             }
             f[i] = v;
         }
@@ -968,7 +1035,8 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
     for (int d = 0; d < D; ++d) j[d] = r0 * u[d * N + node];
     for (int d = 0; d < D; ++d) F[d] = ffield ? double(ffield[d * N + node]) : a.F[d];
     const double dr = drho[node];
-    // first-order viscous non-equilibrium moments of the given gradient (eq. (YuLuobasis))
+    // first-order viscous non-equilibrium moments of the given gradient (D3Q19: eq. (YuLuobasis);
+    // D2Q9 and D3Q15: the same first-order Chapman-Enskog moments worked out on their bases)
     double mn[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) mn[k] = 0.0;
@@ -1004,6 +1072,13 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
             mn[13] = -(G[1][0] + G[0][1]) / (3.0 * snu);
             mn[14] = -(G[2][1] + G[1][2]) / (3.0 * snu);
             mn[15] = -(G[0][2] + G[2][0]) / (3.0 * snu);
+        } else if constexpr (Q == 15) {
+            mn[1] = -2.0 / (3.0 * a.s[1]) * divj;
+            mn[9] = -2.0 / (3.0 * snu) * (3.0 * G[0][0] - divj);
+            mn[10] = -2.0 / (3.0 * snu) * (G[1][1] - G[2][2]);
+            mn[11] = -(G[1][0] + G[0][1]) / (3.0 * snu);
+            mn[12] = -(G[2][1] + G[1][2]) / (3.0 * snu);
+            mn[13] = -(G[0][2] + G[2][0]) / (3.0 * snu);
         } else {
             mn[1] = -2.0 * divj / a.s[1];
             mn[7] = -2.0 * (G[0][0] - G[1][1]) / (3.0 * snu);
@@ -1020,7 +1095,7 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
     const int pos[3] = {x, y, z};
     sfor<Q>([&](auto i) {
         constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
-        const double w = L::w36(CV(i)) / 36.0;
+        const double w = double(L::wnum(CV(i))) / L::WDEN;
         const double cj = cx * j[0] + cy * j[1] + cz * j[2];
         const double cF = cx * F[0] + cy * F[1] + cz * F[2];
         const double feq = w * (dr + 3.0 * cj + 4.5 * cj * cj * ir0 - 1.5 * jj);

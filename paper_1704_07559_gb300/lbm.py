@@ -17,7 +17,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
-D2Q9, D3Q19 = 9, 19
+D2Q9, D3Q15, D3Q19 = 9, 15, 19
 PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2, "bf16s": 3}
 CLOSURE = {"newton": 0, "smag": 1, "powerlaw": 2}
 FORMULA = {"yu": 0, "chai": 1}
@@ -119,8 +119,8 @@ class Lattice:
                  device="cuda", stream=None):
         L = lib()
         self.q = int(lattice)
-        self.d = 3 if self.q == D3Q19 else 2
-        self.ns = 6 if self.q == D3Q19 else 3
+        self.d = 2 if self.q == D2Q9 else 3
+        self.ns = 3 if self.q == D2Q9 else 6
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.shape = (self.nz, self.ny, self.nx)

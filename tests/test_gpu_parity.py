@@ -30,6 +30,8 @@ def rates(q, tau):
     if q == 19:
         return [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / tau, 1.4, 1 / tau, 1.4, 1 / tau, 1 / tau, 1 / tau, 1.98,
                 1.98, 1.98]
+    if q == 15:
+        return [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / tau, 1 / tau, 1 / tau, 1 / tau, 1 / tau, 1.98]
     return [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / tau, 1 / tau]
 
 
@@ -46,7 +48,7 @@ class Case:
     def __init__(self, q, dims, precision="fp32", closure="newton", formula="yu", tau=0.6, bc=None, lid=None,
                  force=None, force_field=False, smag_cs=0.17, pl=(1.0, 0.0), seed=0):
         self.q, self.dims, self.precision = q, dims, precision
-        self.d = 3 if q == 19 else 2
+        self.d = 2 if q == 9 else 3
         self.shape = (dims[2], dims[1], dims[0])
         self.bc = list(bc or ["periodic"] * 6)
         self.bc += ["periodic"] * (6 - len(self.bc))
@@ -148,6 +150,14 @@ CASES = [
     (9, (150, 37, 1), "fp32", "powerlaw", "yu", dict(pl=(0.5, 7e-4), tau=1.0)),
     (9, (97, 40, 1), "fp32", "smag", "yu", dict(force=[1e-5, 2e-6])),
     (9, (97, 40, 1), "fp64", "newton", "chai", dict(force_field=True)),
+    (15, (150, 7, 5), "fp64", "smag", "yu", dict(force=[1e-5, -2e-5, 3e-6], tau=0.55)),
+    (15, (37, 6, 9), "fp64", "newton", "chai", dict(bc=["wall"] * 5 + ["lid"], lid={5: (0.05, 0.02, 0.0)})),
+    (15, (130, 9, 6), "fp32", "smag", "yu", dict(bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+                                                  force=[1e-5, 0, 0], tau=0.51)),
+    (15, (130, 9, 6), "fp32", "smag", "chai", dict(bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+                                                    force=[1e-5, 0, 0], tau=0.51)),
+    (15, (33, 17, 5), "fp32", "powerlaw", "chai", dict(force_field=True, pl=(0.7, 0.01), tau=0.7)),
+    (15, (11, 10, 9), "fp32", "newton", "yu", dict(bc=["wall"] * 4 + ["periodic"] * 2)),
 ]
 
 
@@ -162,34 +172,37 @@ def test_step_parity(q, dims, precision, closure, formula, extra):
     c.check_sums()
 
 
-def test_fp64_trajectory_matches_oracle():
+@pytest.mark.parametrize("q", [19, 15])
+def test_fp64_trajectory_matches_oracle(q):
     """Twenty FP64 steps run independently on both sides stay within 1e-12 (TGV, Smagorinsky)."""
     n = 12
     drho, u, g = I.taylor_green_3d(n, u0=0.04, pressure=True)
-    r = rates(19, 0.51)
+    r = rates(q, 0.51)
     for formula in ("yu", "chai"):
-        lat = lbm.Lattice(19, n, n, n, rates=r, precision="fp64", closure="smag", smag_cs=0.17, formula=formula)
+        lat = lbm.Lattice(q, n, n, n, rates=r, precision="fp64", closure="smag", smag_cs=0.17, formula=formula)
         lat.init(drho, u, g).step(20)
-        G = O.Grid(O.make_params(19, r, closure=O.SMAG, smag_cs=0.17, formula=O.YU if formula == "yu" else O.CHAI),
+        G = O.Grid(O.make_params(q, r, closure=O.SMAG, smag_cs=0.17, formula=O.YU if formula == "yu" else O.CHAI),
                    n, n, n)
         fo = G.run(G.init(drho, u, g), 20)
         assert relerr(f64(lat.get_state()), fo) <= 1e-12
         assert relerr(f64(lat.strain_rate("yu")), G.readout(fo)["S"]) <= 1e-12
 
 
+@pytest.mark.parametrize("q", [19, 15])
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 5, 3), (4, 1, 1), (2, 2, 2)])
-def test_degenerate_periodic_grids(dims):
+def test_degenerate_periodic_grids(dims, q):
     """Grids of extent 1 or 2 on an axis (every neighbour wraps onto the node itself or its twin)."""
-    c = Case(19, dims, "fp64", "smag", "chai", tau=0.55, seed=3)
+    c = Case(q, dims, "fp64", "smag", "chai", tau=0.55, seed=3)
     c.check_init()
     c.check_step()
     c.check_sums()
 
 
-def test_zero_steps_and_yu_equals_chai_on_gpu():
-    """lbm_step(0) leaves the state untouched; on D3Q19 both routes give the same S (Sec. 5.1)
-    on the GPU too, to FP32 rounding."""
-    c = Case(19, (40, 12, 10), "fp32", "smag", "yu", tau=0.51, seed=9)
+@pytest.mark.parametrize("q", [19, 15])
+def test_zero_steps_and_yu_equals_chai_on_gpu(q):
+    """lbm_step(0) leaves the state untouched; both routes give the same S (Sec. 5.1 on D3Q19,
+    the Sec. 5.4 Yu-type formula on D3Q15) on the GPU too, to FP32 rounding."""
+    c = Case(q, (40, 12, 10), "fp32", "smag", "yu", tau=0.51, seed=9)
     c.lat.init(c.drho, c.u, c.g)
     f0 = f64(c.lat.get_state())
     c.lat.step(0)

@@ -41,6 +41,7 @@ def test_default_params(L):
 
 
 D3 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1.6, 1.4, 1.6, 1.4, 1.6, 1.6, 1.6, 1.98, 1.98, 1.98]
+D15 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1.6, 1.6, 1.6, 1.6, 1.6, 1.98]
 
 
 def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
@@ -49,7 +50,7 @@ def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
     p = lbm.default_params()
     if mutate:
         mutate(p)
-    r = rates if rates is not None else (D3 if lattice == 19 else [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1.6, 1.6])
+    r = rates if rates is not None else {19: D3, 15: D15}.get(lattice, [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1.6, 1.6])
     arr = (ctypes.c_double * len(r))(*r)
     ctx = ctypes.c_void_p()
     rc = L.lbm_create(ctypes.byref(ctx), lattice, dims[0], dims[1], dims[2], arr, None, ctypes.byref(p))
@@ -74,6 +75,10 @@ def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
     dict(mutate=lambda p: (setattr(p, "precision", 2), setattr(p, "closure", 2))),
     dict(lattice=9, mutate=lambda p: setattr(p, "precision", 2)),
     dict(mutate=lambda p: (setattr(p, "closure", 2), setattr(p, "pl_tau_min", 0.5))),
+    dict(lattice=15, mutate=lambda p: setattr(p, "precision", 2)),       # D3Q15: no 16-bit storage
+    dict(lattice=15, rates=D15[:7] + [0.3] + D15[8:]),                  # D3Q15 conserved j_z rate
+    dict(lattice=15, rates=D15[:12] + [1.5] + D15[13:]),                # D3Q15 split viscous rates, Yu
+    dict(lattice=15, dims=(8, 8, 0)),
 ])
 def test_create_rejects_bad_arguments(L, case):
     rc, ctx = create(L, **case)
@@ -86,6 +91,14 @@ def test_chai_accepts_split_viscous_rates_host_checks(L):
     """Chai's formula uses each viscous rate on its own, so split rates pass the host checks
     (the call then needs a GPU for its scratch; without one it reports a CUDA error)."""
     rc, ctx = create(L, rates=D3[:13] + [1.2] + D3[14:], mutate=lambda p: setattr(p, "formula", 1))
+    assert rc in (0, -2, -3)
+    if rc == 0:
+        L.lbm_destroy(ctx)
+
+
+def test_d3q15_host_checks_pass(L):
+    """A valid D3Q15 context passes every host check (then needs a GPU for its scratch)."""
+    rc, ctx = create(L, lattice=15)
     assert rc in (0, -2, -3)
     if rc == 0:
         L.lbm_destroy(ctx)

@@ -17,6 +17,7 @@ from paper_1704_07559_gb300 import build, lbm
 RATES19 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, 1 / 0.51, 1.4, 1 / 0.51, 1.4, 1 / 0.51, 1 / 0.51, 1 / 0.51, 1.98,
            1.98, 1.98]
 RATES9 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / 0.7, 1 / 0.7]
+RATES15 = [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2] + [1 / 0.51] * 5 + [1.98]
 
 
 def entry():
@@ -56,11 +57,14 @@ CASES = [
     dict(q=19, dims=(40, 10, 8), precision="fp64", bc=None, force=None, tol=1e-13),
     dict(q=9, dims=(90, 33, 1), precision="fp32", bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)}, force=None,
          tol=1e-6),
+    dict(q=15, dims=(50, 12, 7), precision="fp32", bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+         force=[1e-5, 0.0, 2e-6], tol=1e-6),
 ]
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("case", CASES, ids=["d3q19-fp32-channel", "d3q19-fp64-periodic", "d2q9-fp32-lid"])
+@pytest.mark.parametrize("case", CASES, ids=["d3q19-fp32-channel", "d3q19-fp64-periodic", "d2q9-fp32-lid",
+                                           "d3q15-fp32-channel"])
 def test_matches_lbm_sums_on_two_calls_in_a_row(case):
     """Two calls in a row (before and after a step, so the scratch holds the first call's
     contents when the second runs) agree with lbm_sums within the sums tolerance of the parity
@@ -70,7 +74,7 @@ def test_matches_lbm_sums_on_two_calls_in_a_row(case):
     fn = entry()
     q = case["q"]
     rng = np.random.default_rng(11)
-    lat = lbm.Lattice(q, *case["dims"], rates=RATES19 if q == 19 else RATES9, precision=case["precision"],
+    lat = lbm.Lattice(q, *case["dims"], rates={19: RATES19, 15: RATES15, 9: RATES9}[q], precision=case["precision"],
                       closure="smag", smag_cs=0.17, bc=case["bc"], lid_u=case.get("lid"), force=case["force"])
     d = lat.d
     lat.init(rng.normal(scale=1e-3, size=lat.shape), rng.normal(scale=0.02, size=(d,) + lat.shape),
