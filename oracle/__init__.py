@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 PERIODIC, WALL, LID = 0, 1, 2
-NEWTON, SMAG, POWERLAW = 0, 1, 2
+NEWTON, SMAG, POWERLAW, SMAG_LAGGED, SMAG_DEV = 0, 1, 2, 3, 4
 YU, CHAI = 0, 1
 
 _lib = None
@@ -40,15 +40,15 @@ def lib():
         _lib.or_strain_yu.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
         _lib.or_strain_chai.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
         pp = ctypes.POINTER(Params)
-        _lib.or_collide.argtypes = [pp, dp, dp, dp, dp, dp, ip]
-        _lib.or_node.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
-                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, ip, dp]
-        _lib.or_step.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
-                                 dp, dp, dp, dp, dp]
+        _lib.or_collide.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, ip, dp]
+        _lib.or_node.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, ip, dp, dp]
+        _lib.or_step.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp,
+                                 dp, dp, dp, dp, dp, dp]
         _lib.or_init.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp,
-                                 ctypes.c_int, dp]
+                                 ctypes.c_int, dp, dp]
         _lib.or_readout.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
-                                    dp, dp, dp, dp]
+                                    dp, dp, dp, dp, dp]
         _lib.or_sums.argtypes = [pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, dp]
     return _lib
 
@@ -171,16 +171,20 @@ def make_params(q, rates, closure=NEWTON, formula=YU, rho0=1.0, bc=None, lid_u=N
     return p
 
 
-def collide(p, fin, F=None):
-    """Collision of one node: returns (fout, S, tau, iters)."""
+def collide(p, fin, F=None, tau_prev=0.0, with_next=False):
+    """Collision of one node: returns (fout, S, tau, iters) and, with with_next, the tau to store
+    for the next step.  tau_prev: the node's stored tau (lagged closure)."""
     q = p.q
     fout = np.zeros(q)
     S = np.zeros(n_strain(q))
     tau = ctypes.c_double()
     it = ctypes.c_int()
+    tn = ctypes.c_double()
     Fv = None if F is None else _vec3(F)
-    lib().or_collide(ctypes.byref(p), _dp(_f64(fin)), _dp(Fv), _dp(fout), _dp(S), ctypes.byref(tau),
-                     ctypes.byref(it))
+    lib().or_collide(ctypes.byref(p), _dp(_f64(fin)), _dp(Fv), float(tau_prev), _dp(fout), _dp(S),
+                     ctypes.byref(tau), ctypes.byref(it), ctypes.byref(tn))
+    if with_next:
+        return fout, S, tau.value, it.value, tn.value
     return fout, S, tau.value, it.value
 
 
@@ -204,57 +208,73 @@ class Grid:
         assert F.shape == (self.d,) + self.shape
         return F, 1
 
-    def init(self, drho, u, grad_u=None, force=None):
-        """Post-collision buffer of step -1 whose pull gives the requested pre-collision state."""
+    def init(self, drho, u, grad_u=None, force=None, with_tau=False):
+        """Post-collision buffer of step -1 whose pull gives the requested pre-collision state;
+        with_tau: also each node's closure tau at the prescribed gradient (the lagged closure's
+        first stored tau), returned as (fpost, tau)."""
         fpost = np.zeros((self.q,) + self.shape)
+        tau = np.zeros(self.shape)
         F, ff = self._force(force)
         rc = lib().or_init(ctypes.byref(self.p), self.nx, self.ny, self.nz, _dp(_f64(drho)), _dp(_f64(u)),
-                           _dp(_f64(grad_u)), _dp(F), ff, _dp(fpost))
+                           _dp(_f64(grad_u)), _dp(F), ff, _dp(fpost), _dp(tau))
         if rc != 0:
             raise ValueError("or_init rejected the arguments")
-        return fpost
+        return (fpost, tau) if with_tau else fpost
 
-    def step(self, fpost, force=None, want=()):
-        """One time step.  want: any of 'S', 'tau', 'drho', 'u' (pre-collision state of this step)."""
+    def step(self, fpost, force=None, want=(), tau=None):
+        """One time step.  want: any of 'S', 'tau', 'drho', 'u' (pre-collision state of this step)
+        and 'tau_next' (the taus the next step reads).  tau: the stored tau per node (lagged
+        closure)."""
         fnew = np.zeros_like(fpost)
         F, ff = self._force(force)
         out = {}
         S = np.zeros((n_strain(self.q),) + self.shape) if "S" in want else None
-        tau = np.zeros(self.shape) if "tau" in want else None
+        tau_o = np.zeros(self.shape) if "tau" in want else None
         drho = np.zeros(self.shape) if "drho" in want else None
         u = np.zeros((self.d,) + self.shape) if "u" in want else None
+        tn = np.zeros(self.shape) if "tau_next" in want else None
         rc = lib().or_step(ctypes.byref(self.p), self.nx, self.ny, self.nz, _dp(_f64(fpost)), _dp(F), ff,
-                           _dp(fnew), _dp(S), _dp(tau), _dp(drho), _dp(u))
+                           _dp(_f64(tau)), _dp(fnew), _dp(S), _dp(tau_o), _dp(drho), _dp(u), _dp(tn))
         if rc != 0:
             raise ValueError("or_step rejected the arguments")
-        for k, v in (("S", S), ("tau", tau), ("drho", drho), ("u", u)):
+        for k, v in (("S", S), ("tau", tau_o), ("drho", drho), ("u", u), ("tau_next", tn)):
             if v is not None:
                 out[k] = v
         return fnew, out
 
-    def run(self, fpost, n, force=None):
+    def run(self, fpost, n, force=None, tau=None):
+        """n steps; with a stored tau field (lagged closure) returns (fpost, tau)."""
         for _ in range(n):
-            fpost, _ = self.step(fpost, force)
-        return fpost
+            if tau is None:
+                fpost, _ = self.step(fpost, force)
+            else:
+                fpost, out = self.step(fpost, force, want=("tau_next",), tau=tau)
+                tau = out["tau_next"]
+        return fpost if tau is None else (fpost, tau)
 
-    def readout(self, fpost, force=None):
+    def readout(self, fpost, force=None, tau=None):
         """S, tau, drho, u of the pre-collision state that the next step would see."""
-        _, out = self.step(fpost, force, want=("S", "tau", "drho", "u"))
+        _, out = self.step(fpost, force, want=("S", "tau", "drho", "u"), tau=tau)
         return out
 
-    def node(self, fpost, x, y, z=0, force=None):
-        """(fout, S, tau, iters, fin) of one node of the next step, without touching the grid."""
+    def node(self, fpost, x, y, z=0, force=None, tau=None, with_next=False):
+        """(fout, S, tau, iters, fin) of one node of the next step, without touching the grid
+        (with_next: also the node's tau for the next step).  tau: stored taus (lagged closure)."""
         F, ff = self._force(force)
         fout = np.zeros(self.q)
         S = np.zeros(n_strain(self.q))
         fin = np.zeros(self.q)
-        tau = ctypes.c_double()
+        tau_o = ctypes.c_double()
         it = ctypes.c_int()
+        tn = ctypes.c_double()
         rc = lib().or_node(ctypes.byref(self.p), self.nx, self.ny, self.nz, _dp(_f64(fpost)), _dp(F), ff,
-                           x, y, z, _dp(fout), _dp(S), ctypes.byref(tau), ctypes.byref(it), _dp(fin))
+                           _dp(_f64(tau)), x, y, z, _dp(fout), _dp(S), ctypes.byref(tau_o), ctypes.byref(it),
+                           _dp(fin), ctypes.byref(tn))
         if rc != 0:
             raise ValueError("or_node rejected the arguments")
-        return fout, S, tau.value, it.value, fin
+        if with_next:
+            return fout, S, tau_o.value, it.value, fin, tn.value
+        return fout, S, tau_o.value, it.value, fin
 
     def sums(self, fpost, force=None):
         out = np.zeros(1 + self.d)
@@ -267,4 +287,5 @@ class Grid:
 
 
 __all__ = ["tables", "feq", "meq", "force_bar", "strain_yu", "strain_chai", "make_params", "collide",
-           "Grid", "PERIODIC", "WALL", "LID", "NEWTON", "SMAG", "POWERLAW", "YU", "CHAI", "n_strain"]
+           "Grid", "PERIODIC", "WALL", "LID", "NEWTON", "SMAG", "POWERLAW", "SMAG_LAGGED", "SMAG_DEV", "YU", "CHAI",
+           "n_strain"]

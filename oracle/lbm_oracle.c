@@ -35,7 +35,10 @@
  *     non-equilibrium (f - f_eq + Fbar/2).
  *   - Closures: Smagorinsky tau = tau0 + 3 Cs^2 |S|, power law tau = 1/2 + 3 K |S|^(n-1)
  *     clamped, |S| = sqrt(2 S:S); both solved per node by fixed-point iteration on tau with
- *     S recomputed from the same pre-collision state.
+ *     S recomputed from the same pre-collision state.  Two Smagorinsky variants: lagged (the
+ *     collision uses the tau that the previous step stored at the node, and stores
+ *     tau0 + 3 Cs^2 |S| for the next one) and deviatoric (tau = tau0 + 3 Cs^2 |S_d| with S_d the
+ *     traceless part of S, solved to convergence).
  *   - Boundaries: periodic, halfway bounce-back wall, moving wall (Ladd momentum term).
  *   - Viscosity: nu = (tau - 1/2)/3.
  */
@@ -53,6 +56,8 @@
 #define CL_NEWTON 0
 #define CL_SMAG 1
 #define CL_POWERLAW 2
+#define CL_SMAG_LAGGED 3
+#define CL_SMAG_DEV 4
 
 #define F_YU 0
 #define F_CHAI 1
@@ -470,6 +475,21 @@ static double strain_norm(int q, const double *S) {
     return sqrt(2.0 * ss);
 }
 
+/* |S_d| = sqrt(2 S_d:S_d), S_d = S - tr(S)/d I (the traceless part). */
+static double dev_norm(int q, const double *S) {
+    double ss;
+    if (q != 9) {
+        double t = (S[0] + S[1] + S[2]) / 3.0;
+        double a = S[0] - t, b = S[1] - t, c = S[2] - t;
+        ss = a * a + b * b + c * c + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]);
+    } else {
+        double t = (S[0] + S[1]) / 2.0;
+        double a = S[0] - t, b = S[1] - t;
+        ss = a * a + b * b + 2.0 * S[2] * S[2];
+    }
+    return sqrt(2.0 * ss);
+}
+
 /* S of the current node for a given s_nu (all s_nu entries set to snu), by the chosen route.
  * mneq: effective non-equilibrium moments; fneq: effective non-equilibrium distributions. */
 static void strain_at(const or_params *p, const lattice_t *L, const double *mneq, const double *fneq,
@@ -483,10 +503,37 @@ static void strain_at(const or_params *p, const lattice_t *L, const double *mneq
         or_strain_chai(L->q, fneq, s, p->rho0, S);
 }
 
-/* Solve the closure for tau at one node; returns the number of sweeps taken. */
+/* Solve the closure for tau at one node; returns the number of sweeps taken.
+ * tau_prev: the tau stored at the node by the previous step (read by the lagged closure only);
+ * *tau_next: the tau to store for the next step (lagged: tau0 + 3 Cs^2 |S|; others: tau). */
 static int solve_tau(const or_params *p, const lattice_t *L, const double *mneq, const double *fneq,
-                     double *tau_out, double *S) {
+                     double tau_prev, double *tau_out, double *S, double *tau_next) {
     double tau0 = 1.0 / p->s[L->nu_idx[0]];
+    double c3 = 3.0 * p->smag_cs * p->smag_cs;
+    *tau_next = tau0;
+    if (p->closure == CL_SMAG_LAGGED) {
+        strain_at(p, L, mneq, fneq, 1.0 / tau_prev, S);
+        *tau_out = tau_prev;
+        *tau_next = tau0 + c3 * strain_norm(L->q, S);
+        return 0;
+    }
+    if (p->closure == CL_SMAG_DEV) {
+        /* fixed point tau = tau0 + 3 Cs^2 |S_d(1/tau)| to a relative change of 1e-15 */
+        double tau = tau0;
+        int it;
+        for (it = 1; it <= 200; ++it) {
+            strain_at(p, L, mneq, fneq, 1.0 / tau, S);
+            double tn = tau0 + c3 * dev_norm(L->q, S);
+            double diff = fabs(tn - tau);
+            tau = tn;
+            if (diff <= 1e-15 * tn) break;
+        }
+        if (it > 200) it = 200;
+        strain_at(p, L, mneq, fneq, 1.0 / tau, S);
+        *tau_out = tau;
+        *tau_next = tau;
+        return it;
+    }
     if (p->closure == CL_NEWTON) {
         /* rates used as given (the s_nu entries may differ from each other on the Chai route) */
         if (p->formula == F_YU)
@@ -504,6 +551,7 @@ static int solve_tau(const or_params *p, const lattice_t *L, const double *mneq,
         }
         strain_at(p, L, mneq, fneq, 1.0 / tau, S);
         *tau_out = tau;
+        *tau_next = tau;
         return p->smag_iters;
     }
     /* power law: nu = K |S|^(n-1), tau = 1/2 + 3 nu, clamped to [tau_min, tau_max] */
@@ -522,15 +570,18 @@ static int solve_tau(const or_params *p, const lattice_t *L, const double *mneq,
     if (it > p->pl_max_iter) it = p->pl_max_iter;
     strain_at(p, L, mneq, fneq, 1.0 / tau, S);
     *tau_out = tau;
+    *tau_next = tau;
     return it;
 }
 
 /* One collision at one node (eq. (mrteqvT) with the force source):
- *   fin: pre-collision populations (already pulled), F: force density at the node (d comps).
+ *   fin: pre-collision populations (already pulled), F: force density at the node (d comps),
+ *   tau_prev: the node's stored tau (lagged closure only; ignored otherwise).
  *   fout: post-collision populations; S: strain rate (n_strain comps) of the pre-collision state
- *   with the converged closure; tau: the effective tau; iters: closure sweeps. */
-int or_collide(const or_params *p, const double *fin, const double *F, double *fout, double *S,
-               double *tau_out, int *iters_out) {
+ *   with the converged closure; tau: the effective tau; iters: closure sweeps; tau_next: the tau
+ *   to store for the next step (may be NULL). */
+int or_collide(const or_params *p, const double *fin, const double *F, double tau_prev, double *fout,
+               double *S, double *tau_out, int *iters_out, double *tau_next) {
     const lattice_t *L = lattice(p->q);
     if (!L) return OR_ERR_ARG;
     const int q = L->q;
@@ -565,8 +616,8 @@ int or_collide(const or_params *p, const double *fin, const double *F, double *f
     for (int k = 0; k < q; ++k) mneq[k] = m[k] - meq[k] + 0.5 * TF[k];
     for (int i = 0; i < q; ++i) fneq[i] = fin[i] - feq[i] + 0.5 * Fbar[i];
 
-    double Sl[6] = {0, 0, 0, 0, 0, 0}, tau = 0.0;
-    int iters = solve_tau(p, L, mneq, fneq, &tau, Sl);
+    double Sl[6] = {0, 0, 0, 0, 0, 0}, tau = 0.0, tnext = 0.0;
+    int iters = solve_tau(p, L, mneq, fneq, tau_prev, &tau, Sl, &tnext);
 
     /* rates of this collision */
     double s[19];
@@ -586,6 +637,7 @@ int or_collide(const or_params *p, const double *fin, const double *F, double *f
         for (int c = 0; c < strain_components(q); ++c) S[c] = Sl[c];
     if (tau_out) *tau_out = tau;
     if (iters_out) *iters_out = iters;
+    if (tau_next) *tau_next = tnext;
     return OR_OK;
 }
 
@@ -642,10 +694,12 @@ static double pull(const or_params *p, const lattice_t *L, const double *fpost, 
 
 /* Collide one node of the grid from the post-collision buffer fpost (pull), without writing
  * the grid: used for whole steps and for sampled comparisons at large sizes.
- * force: NULL (none), or d values (uniform) when force_field == 0, or a d x N field. */
+ * force: NULL (none), or d values (uniform) when force_field == 0, or a d x N field.
+ * tau_field: the stored tau of every node (N values; read by the lagged closure, which requires
+ * it); tau_next: the node's tau for the next step (may be NULL). */
 int or_node(const or_params *p, int nx, int ny, int nz, const double *fpost, const double *force,
-            int force_field, int x, int y, int z, double *fout, double *S, double *tau, int *iters,
-            double *fin_out) {
+            int force_field, const double *tau_field, int x, int y, int z, double *fout, double *S,
+            double *tau, int *iters, double *fin_out, double *tau_next) {
     if (check_grid(p, nx, ny, nz) != OR_OK) return OR_ERR_ARG;
     const lattice_t *L = lattice(p->q);
     long N = (long)nx * ny * nz;
@@ -657,13 +711,18 @@ int or_node(const or_params *p, int nx, int ny, int nz, const double *fpost, con
     }
     if (fin_out)
         for (int i = 0; i < L->q; ++i) fin_out[i] = fin[i];
-    return or_collide(p, fin, F, fout, S, tau, iters);
+    if (p->closure == CL_SMAG_LAGGED && !tau_field) return OR_ERR_ARG;
+    double tp = tau_field ? tau_field[idx3(nx, ny, x, y, z)] : 0.0;
+    return or_collide(p, fin, F, tp, fout, S, tau, iters, tau_next);
 }
 
 /* One full time step: fnew = collide(pull(fpost)).  Optional outputs of the pre-collision state
- * of this step: S (n_strain x N), tau (N), macroscopic drho (N) and u (d x N). */
+ * of this step: S (n_strain x N), tau (N), macroscopic drho (N) and u (d x N).
+ * tau_field (N, lagged closure): the stored tau per node; tau_next (N, optional): the taus the
+ * next step reads (may alias tau_field: each node reads only its own entry before writing it). */
 int or_step(const or_params *p, int nx, int ny, int nz, const double *fpost, const double *force,
-            int force_field, double *fnew, double *S, double *tau, double *drho, double *u) {
+            int force_field, const double *tau_field, double *fnew, double *S, double *tau, double *drho,
+            double *u, double *tau_next) {
     if (check_grid(p, nx, ny, nz) != OR_OK) return OR_ERR_ARG;
     const lattice_t *L = lattice(p->q);
     long N = (long)nx * ny * nz;
@@ -672,9 +731,12 @@ int or_step(const or_params *p, int nx, int ny, int nz, const double *fpost, con
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 long n = idx3(nx, ny, x, y, z);
-                double fout[19], Sl[6], t, fin[19];
+                double fout[19], Sl[6], t, fin[19], tn;
                 int it;
-                or_node(p, nx, ny, nz, fpost, force, force_field, x, y, z, fout, Sl, &t, &it, fin);
+                int rc = or_node(p, nx, ny, nz, fpost, force, force_field, tau_field, x, y, z, fout, Sl, &t, &it,
+                                 fin, &tn);
+                if (rc != OR_OK) return rc;
+                if (tau_next) tau_next[n] = tn;
                 for (int i = 0; i < L->q; ++i) fnew[(long)i * N + n] = fout[i];
                 if (S)
                     for (int c = 0; c < ns; ++c) S[(long)c * N + n] = Sl[c];
@@ -696,6 +758,24 @@ int or_step(const or_params *p, int nx, int ny, int nz, const double *fpost, con
     return OR_OK;
 }
 
+/* tau that the closure assigns to a given strain rate S (not formed from populations) */
+static double closure_tau_at(const or_params *p, const lattice_t *L, const double *S) {
+    double tau0 = 1.0 / p->s[L->nu_idx[0]];
+    double c3 = 3.0 * p->smag_cs * p->smag_cs;
+    switch (p->closure) {
+        case CL_SMAG:
+        case CL_SMAG_LAGGED: return tau0 + c3 * strain_norm(L->q, S);
+        case CL_SMAG_DEV: return tau0 + c3 * dev_norm(L->q, S);
+        case CL_POWERLAW: {
+            double tau = 0.5 + 3.0 * p->pl_k * pow(strain_norm(L->q, S), p->pl_n - 1.0);
+            if (!(tau >= p->pl_tau_min)) tau = p->pl_tau_min;
+            if (tau > p->pl_tau_max) tau = p->pl_tau_max;
+            return tau;
+        }
+        default: return tau0;
+    }
+}
+
 /* Initial state from macroscopic fields (Sec. 4.1, eq. (YuLuobasis)):
  *   pre-collision f(x, 0) = f_eq(drho, rho0 u) + T^-1 m_neq(grad u) - Fbar/2,
  * where m_neq holds only the first-order viscous moments.  D3Q19:
@@ -711,9 +791,10 @@ int or_step(const or_params *p, int nx, int ny, int nz, const double *fpost, con
  * s_nu is the closure's value for the given gradient (explicit, since S is given).
  * grad_u: d*d x N, entry (a*d + b) = d u_a / d x_b; NULL for a pure equilibrium.
  * The buffer written is the post-collision state of step -1: f(x,0) is un-streamed so that the
- * next pull returns exactly f(x,0). */
+ * next pull returns exactly f(x,0).  tau_field (N, may be NULL) receives each node's closure tau
+ * at the prescribed gradient (the lagged closure's first stored tau). */
 int or_init(const or_params *p, int nx, int ny, int nz, const double *drho, const double *u,
-            const double *grad_u, const double *force, int force_field, double *fpost) {
+            const double *grad_u, const double *force, int force_field, double *fpost, double *tau_field) {
     if (check_grid(p, nx, ny, nz) != OR_OK) return OR_ERR_ARG;
     const lattice_t *L = lattice(p->q);
     const int q = L->q, d = L->d;
@@ -730,36 +811,28 @@ int or_init(const or_params *p, int nx, int ny, int nz, const double *drho, cons
                 or_feq(q, drho[n], j, p->rho0, feq);
                 or_force_bar(q, j, p->rho0, F, Fbar);
                 for (int k = 0; k < q; ++k) mneq[k] = 0.0;
+                double G[3][3] = {{0}}, Sx[6] = {0, 0, 0, 0, 0, 0};
                 if (grad_u) {
-                    double G[3][3] = {{0}};
                     for (int a = 0; a < d; ++a)
                         for (int b = 0; b < d; ++b) G[a][b] = p->rho0 * grad_u[(long)(a * d + b) * N + n];
-                    /* closure value of s_nu at this gradient */
-                    double Sx[6];
-                    double snu = p->s[L->nu_idx[0]];
-                    if (p->closure != CL_NEWTON) {
-                        if (d == 3) {
-                            Sx[0] = G[0][0] / p->rho0;
-                            Sx[1] = G[1][1] / p->rho0;
-                            Sx[2] = G[2][2] / p->rho0;
-                            Sx[3] = 0.5 * (G[0][1] + G[1][0]) / p->rho0;
-                            Sx[4] = 0.5 * (G[1][2] + G[2][1]) / p->rho0;
-                            Sx[5] = 0.5 * (G[0][2] + G[2][0]) / p->rho0;
-                        } else {
-                            Sx[0] = G[0][0] / p->rho0;
-                            Sx[1] = G[1][1] / p->rho0;
-                            Sx[2] = 0.5 * (G[0][1] + G[1][0]) / p->rho0;
-                        }
-                        double g = strain_norm(q, Sx), tau;
-                        if (p->closure == CL_SMAG) {
-                            tau = 1.0 / p->s[L->nu_idx[0]] + 3.0 * p->smag_cs * p->smag_cs * g;
-                        } else {
-                            tau = 0.5 + 3.0 * p->pl_k * pow(g, p->pl_n - 1.0);
-                            if (!(tau >= p->pl_tau_min)) tau = p->pl_tau_min;
-                            if (tau > p->pl_tau_max) tau = p->pl_tau_max;
-                        }
-                        snu = 1.0 / tau;
+                    if (d == 3) {
+                        Sx[0] = G[0][0] / p->rho0;
+                        Sx[1] = G[1][1] / p->rho0;
+                        Sx[2] = G[2][2] / p->rho0;
+                        Sx[3] = 0.5 * (G[0][1] + G[1][0]) / p->rho0;
+                        Sx[4] = 0.5 * (G[1][2] + G[2][1]) / p->rho0;
+                        Sx[5] = 0.5 * (G[0][2] + G[2][0]) / p->rho0;
+                    } else {
+                        Sx[0] = G[0][0] / p->rho0;
+                        Sx[1] = G[1][1] / p->rho0;
+                        Sx[2] = 0.5 * (G[0][1] + G[1][0]) / p->rho0;
                     }
+                }
+                /* the closure's tau at the prescribed strain rate (explicit, since S is given) */
+                double tau_i = closure_tau_at(p, L, Sx);
+                if (tau_field) tau_field[n] = tau_i;
+                if (grad_u) {
+                    double snu = p->closure == CL_NEWTON ? p->s[L->nu_idx[0]] : 1.0 / tau_i;
                     double divj = 0.0;
                     for (int a = 0; a < d; ++a) divj += G[a][a];
                     if (q == 19) {
@@ -822,13 +895,13 @@ int or_init(const or_params *p, int nx, int ny, int nz, const double *drho, cons
 /* Read-outs of the pre-collision state of the next step (pull from fpost):
  * strain rate by either formula with the converged closure, and macroscopic fields. */
 int or_readout(const or_params *p, int nx, int ny, int nz, const double *fpost, const double *force,
-               int force_field, double *S, double *tau, double *drho, double *u) {
+               int force_field, const double *tau_field, double *S, double *tau, double *drho, double *u) {
     if (check_grid(p, nx, ny, nz) != OR_OK) return OR_ERR_ARG;
     long N = (long)nx * ny * nz;
     int q = p->q;
     double *scratch = (double *)malloc(sizeof(double) * (size_t)q * (size_t)N);
     if (!scratch) return OR_ERR_ARG;
-    int rc = or_step(p, nx, ny, nz, fpost, force, force_field, scratch, S, tau, drho, u);
+    int rc = or_step(p, nx, ny, nz, fpost, force, force_field, tau_field, scratch, S, tau, drho, u, NULL);
     free(scratch);
     return rc;
 }

@@ -286,13 +286,13 @@ def test_initial_strain_equals_analytic(q):
     else:
         cases = [I.taylor_green_2d(12, 12, u0=0.03)]
         dims = (12, 12, 1)
-    for closure in (O.NEWTON, O.SMAG):
+    for closure in (O.NEWTON, O.SMAG, O.SMAG_LAGGED, O.SMAG_DEV):
         for drho, u, g in cases:
             for formula in (O.YU, O.CHAI):
                 p = O.make_params(q, rates(q), formula=formula, closure=closure, smag_cs=0.17)
                 G = O.Grid(p, *dims)
-                f = G.init(drho, u, g)
-                r = G.readout(f)
+                f, tau = G.init(drho, u, g, with_tau=True)
+                r = G.readout(f, tau=tau)
                 Sa = strain_from_grad(q, g)
                 assert np.abs(r["S"] - Sa).max() < 1e-14 * np.abs(Sa).max()
                 assert np.abs(r["u"] - u).max() < 1e-16
@@ -408,3 +408,112 @@ def test_couette_moving_lid(q):
     assert np.abs(r["S"][ixy] - U / (2 * H)).max() < 1e-9 * U / (2 * H)
     y = np.arange(H)
     assert np.abs(r["u"][0, 0, :, 0] - U * (y + 0.5) / H).max() < 1e-9 * U
+
+
+# ------------------------------------------------------------------------------------------------
+# Smagorinsky variants: lagged (tau stored from the previous step) and deviatoric (|S_d|)
+
+
+def dev_norm(S):
+    """|S_d| of 3D strain arrays (6, ...), S_d = S - tr(S)/3 I."""
+    t = (S[0] + S[1] + S[2]) / 3
+    return np.sqrt(2 * ((S[0] - t) ** 2 + (S[1] - t) ** 2 + (S[2] - t) ** 2 + 2 * (S[3] ** 2 + S[4] ** 2 + S[5] ** 2)))
+
+
+@pytest.mark.parametrize("closure", [O.SMAG_LAGGED, O.SMAG_DEV])
+def test_smagorinsky_variants_with_zero_constant_are_newtonian(closure):
+    n = 6
+    drho, u, g = I.taylor_green_3d(n, u0=0.03, pressure=True)
+    pn = O.make_params(19, rates(19, 0.51))
+    pv = O.make_params(19, rates(19, 0.51), closure=closure, smag_cs=0.0)
+    Gn, Gv = O.Grid(pn, n, n, n), O.Grid(pv, n, n, n)
+    f, tau = Gv.init(drho, u, g, with_tau=True)
+    assert np.all(tau == 0.51)
+    a = Gn.run(f, 3)
+    b = Gv.run(f, 3, tau=tau) if closure == O.SMAG_LAGGED else Gv.run(f, 3)
+    if closure == O.SMAG_LAGGED:
+        b, tau = b
+        assert np.all(tau == 0.51)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("formula", [O.YU, O.CHAI])
+def test_lagged_closure_reads_the_stored_tau(formula):
+    """One lagged step collides with the stored tau (any field, here a random one) and stores
+    tau0 + 3 Cs^2 |S| of the strain rate formed with it: a Newtonian step with that tau at each
+    node gives the same populations and S."""
+    n, cs = 5, 0.3
+    rng = np.random.default_rng(4)
+    p = O.make_params(19, rates(19, 0.55), closure=O.SMAG_LAGGED, smag_cs=cs, formula=formula)
+    G = O.Grid(p, n, n, n)
+    f = I.random_populations(19, G.shape, scale=2e-3, seed=8)
+    tau = rng.uniform(0.52, 0.9, size=G.shape)
+    fl, out = G.step(f, want=("S", "tau", "tau_next"), tau=tau)
+    assert np.array_equal(out["tau"], tau)
+    Sn = np.sqrt(2 * ((out["S"][:3] ** 2).sum(0) + 2 * (out["S"][3:] ** 2).sum(0)))
+    assert np.abs(out["tau_next"] - (0.55 + 3 * cs * cs * Sn)).max() < 1e-15
+    for k in range(5):  # compare a few nodes against Newtonian collisions at the stored tau
+        x, y, z = rng.integers(n, size=3)
+        pn = O.make_params(19, rates(19, tau[z, y, x]), formula=formula)
+        fo, So, _, _, _ = O.Grid(pn, n, n, n).node(f, x, y, z)
+        assert np.abs(fo - fl[:, z, y, x]).max() < 1e-17
+        assert np.abs(So - out["S"][:, z, y, x]).max() < 1e-17
+
+
+@pytest.mark.parametrize("formula", [O.YU, O.CHAI])
+def test_lagged_and_implicit_reach_the_same_steady_channel(formula):
+    """Force-driven channel with a strong Smagorinsky closure (Cs = 1, g = 1e-5): the lagged
+    closure's steady state is the implicit fixed point (stationary tau satisfies the same
+    equation), and both satisfy the exact steady momentum balance 2 nu_eff S_xy = -g (y - y_c)."""
+    tau0, H, gx, cs = 0.8, 16, 1e-5, 1.0
+    F = np.array([gx, 0.0, 0.0])
+    res = {}
+    for closure in (O.SMAG, O.SMAG_LAGGED):
+        p = O.make_params(19, rates(19, tau0), bc=CHANNEL, formula=formula, closure=closure, smag_cs=cs,
+                          smag_iters=12)
+        G = O.Grid(p, 1, H, 1)
+        f, tau = G.init(np.zeros((1, H, 1)), np.zeros((3, 1, H, 1)), force=F, with_tau=True)
+        if closure == O.SMAG:
+            f = G.run(f, 8000, force=F)
+            r = G.readout(f, force=F)
+        else:
+            f, tau = G.run(f, 8000, force=F, tau=tau)
+            r = G.readout(f, force=F, tau=tau)
+        res[closure] = r
+        y = np.arange(H)
+        nu = (r["tau"][0, :, 0] - 0.5) / 3
+        Sxy = r["S"][3, 0, :, 0]
+        bal = -gx * (y - (H - 1) / 2)
+        assert np.abs(2 * nu * Sxy - bal).max() < 1e-8 * np.abs(bal).max()
+        assert r["tau"].max() > tau0 + 1e-3  # the closure is active
+    a, b = res[O.SMAG], res[O.SMAG_LAGGED]
+    assert np.abs(a["S"] - b["S"]).max() < 1e-9 * np.abs(a["S"]).max()
+    assert np.abs(a["tau"] - b["tau"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("formula", [O.YU, O.CHAI])
+def test_deviatoric_closure(formula):
+    """The deviatoric variant returns the root of tau = tau0 + 3 Cs^2 |S_d(1/tau)|, which is the
+    larger root of the quadratic tau^2 - tau0 tau - 3 Cs^2 |S_d(s = 1)| = 0 (S_d is proportional to
+    s_nu on these bases); it equals the implicit |S| closure when the flow has no bulk strain
+    (divergence-free initial gradient) and never exceeds it."""
+    n, cs, tau0 = 8, 0.17, 0.51
+    drho, u, g = I.taylor_green_3d(n, u0=0.05)
+    pd = O.make_params(19, rates(19, tau0), closure=O.SMAG_DEV, smag_cs=cs, formula=formula)
+    ps = O.make_params(19, rates(19, tau0), closure=O.SMAG, smag_cs=cs, smag_iters=30, formula=formula)
+    Gd, Gs = O.Grid(pd, n, n, n), O.Grid(ps, n, n, n)
+    f = Gd.init(drho, u, g)
+    rd, rs = Gd.readout(f), Gs.readout(f)
+    assert np.abs(rd["tau"] - rs["tau"]).max() < 1e-15
+    assert rd["tau"].max() > tau0 + 1e-3
+    # a general state (bulk strain present)
+    fr = I.random_populations(19, Gd.shape, scale=3e-3, seed=12)
+    rd, rs = Gd.readout(fr), Gs.readout(fr)
+    c3 = 3 * cs * cs
+    assert np.abs(rd["tau"] - (tau0 + c3 * dev_norm(rd["S"]))).max() < 1e-15
+    assert np.all(rd["tau"] <= rs["tau"] + 1e-15)
+    assert np.abs(rd["tau"] - rs["tau"]).max() > 1e-9
+    # closed form: S_d at unit rate is S_d(1/tau) * tau
+    Sd1 = dev_norm(rd["S"]) * rd["tau"]
+    root = 0.5 * (tau0 + np.sqrt(tau0 * tau0 + 4 * c3 * Sd1))
+    assert np.abs(root - rd["tau"]).max() < 1e-15
