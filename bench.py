@@ -9,7 +9,7 @@ traffic (19 populations read + 19 written, 152 bytes per node update) represents
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|fp16s|bf16s|fp64] [--formula yu|chai] [--lattice 19|15]
-                  [--no-variants] [--quick]
+                  [--closure smag|smag_lagged|smag_dev] [--no-variants] [--quick]
 
 --precision / --formula pick the headline (default fp32 / yu); --quick skips the end-to-end
 run, the other variants and the CPU baseline (used for profiler captures).
@@ -43,6 +43,8 @@ BYTES_PER_LUP = {"fp32": 152, "fp64": 304, "fp16s": 76, "bf16s": 76}
 STORAGE_NOTE = {"fp32": "fp32 populations, fp32 arithmetic", "fp64": "fp64 populations, fp64 arithmetic",
                 "fp16s": "fp16 populations (delta-rho form), fp32 arithmetic",
                 "bf16s": "bf16 populations (delta-rho form), fp32 arithmetic"}
+CLOSURE_NOTE = {"smag": "smagorinsky", "smag_lagged": "smagorinsky, tau from the previous step",
+                "smag_dev": "smagorinsky on the traceless strain rate, closed form"}
 WORKLOAD = "D3Q19 MRT Smagorinsky LES channel 256x128x128, walls at y, g_x=1e-6, Cs=0.17, tau0=0.51"
 METRIC = "MLUPS, MRT step + strain rate (Smagorinsky LES channel)"
 
@@ -140,12 +142,12 @@ class ClockSampler:
 # our arm
 
 
-def make_lattice(precision="fp32", formula="yu", dims=(NX, NY, NZ), lattice=19):
+def make_lattice(precision="fp32", formula="yu", dims=(NX, NY, NZ), lattice=19, closure="smag"):
     from paper_1704_07559_gb300 import inputs as I
     from paper_1704_07559_gb300 import lbm
 
     lat = lbm.Lattice(lattice, *dims, rates=RATES if lattice == 19 else RATES15, force=[G, 0.0, 0.0],
-                      precision=precision, closure="smag", smag_cs=CS, formula=formula, bc=BC)
+                      precision=precision, closure=closure, smag_cs=CS, formula=formula, bc=BC)
     drho, u = I.channel_profile(*dims, u_centre=0.1, noise=0.01, seed=2)
     lat.init(drho, u)
     return lat
@@ -241,10 +243,12 @@ def run_ours(args):
 
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    lat = make_lattice(args.precision, args.formula, lattice=args.lattice)
+    lat = make_lattice(args.precision, args.formula, lattice=args.lattice, closure=args.closure)
     N = lat.N
     lname = "D3Q%d" % args.lattice
     bytes_per_lup = BYTES_PER_LUP[args.precision] * args.lattice // 19
+    if args.closure == "smag_lagged":  # the stored tau, read and written
+        bytes_per_lup += 16 if args.precision == "fp64" else 8
 
     # timed region: barrier + synchronize on both sides, max over ranks
     lat.step(args.warmup)
@@ -269,13 +273,14 @@ def run_ours(args):
     k_ms = statistics.mean(per)
     achieved = bytes_per_lup * N / (k_ms * 1e-3) / 1e9
 
-    kernel = "k_step<%s,%s,SMAG,%s,force>" % (lname, args.precision, args.formula.upper())
+    kernel = "k_step<%s,%s,%s,%s,force>" % (lname, args.precision, args.closure.upper(), args.formula.upper())
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("D3Q19", lname), "lattice": lname, "grid": [NX, NY, NZ],
-                   "formula": args.formula, "closure": "smagorinsky", "precision": STORAGE_NOTE[args.precision],
+                   "formula": args.formula, "closure": CLOSURE_NOTE[args.closure],
+                   "precision": STORAGE_NOTE[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (two 319 MB population buffers per step)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -319,6 +324,32 @@ def variants(args, hbm):
         k_ms = statistics.mean(time_steps(lat, n, max(3, args.warmup // 10), per_launch=True))
         res["channel"]["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
         lat.close()
+        torch.cuda.empty_cache()
+    # Smagorinsky variants on the same channel: the lagged closure (tau stored from the previous
+    # step, 8 more bytes per node update) and the deviatoric closure in closed form; their rate,
+    # and their difference from the implicit closure after 1000 steps from the same start
+    T = 1000
+    for formula in ("yu", "chai"):
+        ref = make_lattice("fp32", formula)
+        ref.step(T)
+        _, u_ref = ref.macroscopic()
+        S_ref = ref.strain_rate(formula)
+        ref.close()
+        for closure, extra in (("smag_lagged", 8), ("smag_dev", 0)):
+            lat = make_lattice("fp32", formula, closure=closure)
+            k_ms = statistics.mean(time_steps(lat, steps, max(3, args.warmup // 10), per_launch=True))
+            row = rate(lat.N, k_ms, BYTES_PER_LUP["fp32"] + extra, hbm)
+            lat.close()
+            lat = make_lattice("fp32", formula, closure=closure)
+            lat.step(T)
+            _, u = lat.macroscopic()
+            S = lat.strain_rate(formula)
+            row["u_rel_l2_vs_implicit_t1000"] = float((u - u_ref).norm() / u_ref.norm())
+            row["S_rel_l2_vs_implicit_t1000"] = float((S - S_ref).norm() / S_ref.norm())
+            res["channel"]["fp32_%s_%s" % (formula, closure)] = row
+            lat.close()
+            del u, S
+        del u_ref, S_ref
         torch.cuda.empty_cache()
     # the same channel on D3Q15 (d'Humieres basis; Yu-type formula of the Sec. 5.4 procedure)
     for formula in ("yu", "chai"):
@@ -588,6 +619,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16s", "bf16s", "fp64"])
     ap.add_argument("--formula", default="yu", choices=["yu", "chai"])
+    ap.add_argument("--closure", default="smag", choices=["smag", "smag_lagged", "smag_dev"],
+                    help="the channel's Smagorinsky closure: implicit (default), lagged or deviatoric closed form")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 15],
                     help="19: the D3Q19 channel (default); 15: the same channel on D3Q15 (fp32/fp64 only)")
     ap.add_argument("--no-variants", action="store_true")

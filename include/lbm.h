@@ -67,6 +67,14 @@ extern "C" {
 #define LBM_NEWTON 0   /* tau fixed by the rates given to lbm_create */
 #define LBM_SMAG 1     /* tau = tau0 + 3 Cs^2 |S| (filter width 1) */
 #define LBM_POWERLAW 2 /* tau = 1/2 + 3 K |S|^(n-1), clamped to [tau_min, tau_max] */
+/* Explicit Smagorinsky: each node collides with the tau that the previous step stored for it and
+ * stores tau0 + 3 Cs^2 |S| of the strain rate formed with that tau (a caller-owned tau field, see
+ * lbm_bind_tau).  Its steady states are those of LBM_SMAG. */
+#define LBM_SMAG_LAGGED 3
+/* Smagorinsky on the traceless strain rate: tau = tau0 + 3 Cs^2 |S_d|, S_d = S - tr(S)/d I.  On
+ * these moment bases S_d is proportional to s_nu, so tau is the larger root of a quadratic and is
+ * computed in closed form (no sweeps).  Equal to LBM_SMAG when the flow has no bulk strain. */
+#define LBM_SMAG_DEV 4
 
 /* strain-rate routes */
 #define LBM_YU 0
@@ -83,7 +91,7 @@ extern "C" {
  * sweeps from tau0 until |tau_new - tau| <= pl_tol * tau_new or pl_max_iter sweeps. */
 typedef struct lbm_params {
     int precision;   /* LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S */
-    int closure;     /* LBM_NEWTON, LBM_SMAG, LBM_POWERLAW */
+    int closure;     /* LBM_NEWTON, LBM_SMAG, LBM_POWERLAW, LBM_SMAG_LAGGED, LBM_SMAG_DEV */
     int formula;     /* LBM_YU or LBM_CHAI: the route whose S feeds the closure in lbm_step */
     int smag_iters;  /* Smagorinsky sweeps, 1..64 (default 6) */
     int pl_max_iter; /* power-law sweep cap, 1..1000 (default 64) */
@@ -134,6 +142,16 @@ int lbm_layout(const lbm_ctx* ctx, int* q, int64_t* stride, int* elem_bytes);
  * p->force_field = 1 (must be non-NULL then), else ignored.  The buffers must stay valid until
  * the context is destroyed or re-bound.  After binding, A is the current buffer. */
 int lbm_bind(lbm_ctx* ctx, void* f_a, void* f_b, const void* force_field, void* stream);
+
+/* Bind the tau field of the LBM_SMAG_LAGGED closure: N values of the compute type (double for
+ * LBM_FP64, float otherwise), caller-owned device memory, naturally aligned, valid until the
+ * context is destroyed or re-bound.  lbm_init writes every node's first tau (the closure's value
+ * at the prescribed gradient, tau0 without one); each lbm_step reads a node's entry and rewrites it
+ * in place; read-outs read it.  The caller may read or overwrite it between calls (it is part of
+ * the state: lbm_get_state / lbm_set_state do not copy it).  Other closures ignore it.  With the
+ * lagged closure, lbm_init, lbm_step, lbm_strain_rate and lbm_macroscopic return LBM_ERR_STATE
+ * until it is bound.  Errors: LBM_ERR_ARG for NULL or misaligned memory. */
+int lbm_bind_tau(lbm_ctx* ctx, void* tau_field);
 
 /* Initialise the current buffer so that the next step sees the pre-collision state
  *   f(x) = f_eq(drho, rho0 u) + T^-1 m_neq - Fbar/2,

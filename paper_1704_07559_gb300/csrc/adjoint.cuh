@@ -79,7 +79,7 @@ __device__ __forceinline__ void node_forward(const R (&p)[19], const R (&F)[3], 
     });
     R A[6];
     Eq<D3Q19>::yu_split(st.mn, a.s[1] * R(Eq<D3Q19>::YU_A) * ir0, ir0, A, st.B);
-    st.tau = solve_tau<D3Q19, R, CLOSURE>(A, st.B, a, st.S, st.s);
+    st.tau = solve_tau<D3Q19, R, CLOSURE>(A, st.B, a, st.S, st.s, 0);  // Newtonian / Smagorinsky only
     st.snorm = sqrt(R(2) * strain_w_dot(st.S, st.S));
 }
 

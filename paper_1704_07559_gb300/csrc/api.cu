@@ -25,6 +25,7 @@ struct lbm_ctx {
     // bound resources
     void* buf[2];
     const void* force_field;
+    void* tau_field;  // lagged closure: the stored tau per node (caller-owned)
     cudaStream_t stream;
     int bound;
     int cur;  // index of the current buffer
@@ -119,6 +120,7 @@ void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
     a->wall_mask = wall;
     a->lid_mask = lid;
     a->force_field = c->p.force_field ? static_cast<const R*>(c->force_field) : nullptr;
+    a->tau_field = static_cast<R*>(c->tau_field);
 }
 
 // source / destination buffers and their per-population base pointers
@@ -203,6 +205,8 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
 int check_bound(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
     if (!c->bound) return fail(c, LBM_ERR_STATE, "no buffers bound (call lbm_bind first)");
+    if (c->p.closure == LBM_SMAG_LAGGED && !c->tau_field)
+        return fail(c, LBM_ERR_STATE, "the lagged closure needs its tau field (call lbm_bind_tau first)");
     return LBM_OK;
 }
 
@@ -447,8 +451,9 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
         default: return bad("precision");
     }
     if (tag_of(c->q, p.precision) == T_NONE) return bad("lattice/precision");
-    if (p.closure < LBM_NEWTON || p.closure > LBM_POWERLAW) return bad("closure");
-    if ((p.precision == LBM_FP16S || p.precision == LBM_BF16S) && p.closure == LBM_POWERLAW) return bad("16-bit power law");
+    if (p.closure < LBM_NEWTON || p.closure > LBM_SMAG_DEV) return bad("closure");
+    if ((p.precision == LBM_FP16S || p.precision == LBM_BF16S) && p.closure != LBM_NEWTON && p.closure != LBM_SMAG)
+        return bad("closure for 16-bit storage");
     if (p.formula != LBM_YU && p.formula != LBM_CHAI) return bad("formula");
     if ((p.closure != LBM_NEWTON || p.formula == LBM_YU) && !viscous_rates_equal(c)) return bad("viscous rates");
     if (!(p.rho0 > 0.0) || !is_finite(p.rho0)) return bad("rho0");
@@ -517,6 +522,16 @@ int lbm_bind(lbm_ctx* c, void* f_a, void* f_b, const void* force_field, void* st
     return LBM_OK;
 }
 
+int lbm_bind_tau(lbm_ctx* c, void* tau_field) {
+    if (!c) return LBM_ERR_ARG;
+    if (!tau_field) return fail(c, LBM_ERR_ARG, "lbm_bind_tau: tau field required");
+    if ((uintptr_t)tau_field & (c->p.precision == LBM_FP64 ? 7 : 3))
+        return fail(c, LBM_ERR_ARG, "lbm_bind_tau: misaligned tau field");
+    c->tau_field = tau_field;
+    c->err[0] = '\0';
+    return LBM_OK;
+}
+
 int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad_u) {
     int rc = check_bound(c);
     if (rc) return rc;
@@ -525,31 +540,40 @@ int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad
     fill_args(c, &a);
     set_buffers(c, &a, nullptr, c->buf[c->cur]);
     cudaError_t e;
+    void* tf = c->p.closure == LBM_SMAG_LAGGED ? c->tau_field : nullptr;  // only the lagged closure keeps taus
     const Tag t = tag_of(c->q, c->p.precision);
     switch (t) {
         case T_D3Q19_F64:
-            e = lbm::init_d3q19_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
+            e = lbm::init_d3q19_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field),
+                                    static_cast<double*>(tf), c->stream);
             break;
         case T_D3Q15_F64:
-            e = lbm::init_d3q15_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
+            e = lbm::init_d3q15_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field),
+                                    static_cast<double*>(tf), c->stream);
             break;
         case T_D3Q15_F32:
-            e = lbm::init_d3q15_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            e = lbm::init_d3q15_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
             break;
         case T_D2Q9_F64:
-            e = lbm::init_d2q9_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field), c->stream);
+            e = lbm::init_d2q9_f64(a, c->p.closure, drho, u, grad_u, static_cast<const double*>(c->force_field),
+                                    static_cast<double*>(tf), c->stream);
             break;
         case T_D3Q19_F32:
-            e = lbm::init_d3q19_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            e = lbm::init_d3q19_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
             break;
         case T_D3Q19_F16:
-            e = lbm::init_d3q19_f16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            e = lbm::init_d3q19_f16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
             break;
         case T_D3Q19_BF16:
-            e = lbm::init_d3q19_bf16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            e = lbm::init_d3q19_bf16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
             break;
         case T_D2Q9_F32:
-            e = lbm::init_d2q9_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field), c->stream);
+            e = lbm::init_d2q9_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
             break;
         default: return fail(c, LBM_ERR_ARG, "lbm_init: unsupported lattice/precision");
     }

@@ -70,8 +70,19 @@ cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s
     }
     dim3 g, b;
     lattice_grid(a.nx, a.ny, a.nz, &g, &b);
-    k_step<L, ST, C, F, FO, 1><<<g, b, 0, s>>>(a);
-    return cudaGetLastError();
+    // programmatic dependent launch: consecutive steps overlap launch and block scheduling with
+    // the previous step's tail (k_step waits for the previous kernel before its first load)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step<L, ST, C, F, FO, 1>, a);
 }
 
 template <class L, class ST, int C, int F>
@@ -79,7 +90,9 @@ cudaError_t launch_step_cf(const StepArgs<typename Store<ST>::R>& a, int force, 
     return force ? launch_form<L, ST, C, F, true>(a, s) : launch_form<L, ST, C, F, false>(a, s);
 }
 
-template <class L, class ST, bool POWERLAW_BUILT>
+// EXTRA_CLOSURES: the power law and the two Smagorinsky variants (lagged, deviatoric) are
+// instantiated (FP32 and FP64 storage); 16-bit storage builds Newtonian and Smagorinsky only.
+template <class L, class ST, bool EXTRA_CLOSURES>
 cudaError_t launch_step(const StepArgs<typename Store<ST>::R>& a, int closure, int formula, int force,
                         cudaStream_t s) {
     const bool yu = formula == F_YU;
@@ -91,9 +104,19 @@ cudaError_t launch_step(const StepArgs<typename Store<ST>::R>& a, int closure, i
             return yu ? launch_step_cf<L, ST, CL_SMAG, F_YU>(a, force, s)
                       : launch_step_cf<L, ST, CL_SMAG, F_CHAI>(a, force, s);
         case CL_POWERLAW:
-            if constexpr (POWERLAW_BUILT)
+            if constexpr (EXTRA_CLOSURES)
                 return yu ? launch_step_cf<L, ST, CL_POWERLAW, F_YU>(a, force, s)
                           : launch_step_cf<L, ST, CL_POWERLAW, F_CHAI>(a, force, s);
+            return cudaErrorNotSupported;
+        case CL_SMAG_LAGGED:
+            if constexpr (EXTRA_CLOSURES)
+                return yu ? launch_step_cf<L, ST, CL_SMAG_LAGGED, F_YU>(a, force, s)
+                          : launch_step_cf<L, ST, CL_SMAG_LAGGED, F_CHAI>(a, force, s);
+            return cudaErrorNotSupported;
+        case CL_SMAG_DEV:
+            if constexpr (EXTRA_CLOSURES)
+                return yu ? launch_step_cf<L, ST, CL_SMAG_DEV, F_YU>(a, force, s)
+                          : launch_step_cf<L, ST, CL_SMAG_DEV, F_CHAI>(a, force, s);
             return cudaErrorNotSupported;
         default:
             return cudaErrorInvalidValue;
@@ -102,10 +125,10 @@ cudaError_t launch_step(const StepArgs<typename Store<ST>::R>& a, int closure, i
 
 template <class L, class ST>
 cudaError_t launch_init(const StepArgs<double>& a, int closure, const double* drho, const double* u, const double* gu,
-                        const typename Store<ST>::R* ffield, cudaStream_t s) {
+                        const typename Store<ST>::R* ffield, typename Store<ST>::R* tau_field, cudaStream_t s) {
     dim3 g, b;
     lattice_grid(a.nx, a.ny, a.nz, &g, &b);
-    k_init<L, ST><<<g, b, 0, s>>>(a, closure, drho, u, gu, ffield);
+    k_init<L, ST><<<g, b, 0, s>>>(a, closure, drho, u, gu, ffield, tau_field);
     return cudaGetLastError();
 }
 
@@ -120,15 +143,16 @@ cudaError_t launch_sums(const StepArgs<typename Store<ST>::R>& a, double* partia
 
 }  // namespace lbm
 
-#define LBM_DEFINE_ENTRY(TAG, L, ST, POWERLAW_BUILT)                                                         \
+#define LBM_DEFINE_ENTRY(TAG, L, ST, EXTRA_CLOSURES)                                                         \
     namespace lbm {                                                                                          \
     cudaError_t step_##TAG(const StepArgs<Store<ST>::R>& a, int closure, int formula, int force,             \
                            cudaStream_t s) {                                                                 \
-        return launch_step<L, ST, POWERLAW_BUILT>(a, closure, formula, force, s);                            \
+        return launch_step<L, ST, EXTRA_CLOSURES>(a, closure, formula, force, s);                            \
     }                                                                                                        \
     cudaError_t init_##TAG(const StepArgs<double>& a, int closure, const double* drho, const double* u,      \
-                           const double* gu, const Store<ST>::R* ffield, cudaStream_t s) {                   \
-        return launch_init<L, ST>(a, closure, drho, u, gu, ffield, s);                                       \
+                           const double* gu, const Store<ST>::R* ffield, Store<ST>::R* tau_field,            \
+                           cudaStream_t s) {                                                                 \
+        return launch_init<L, ST>(a, closure, drho, u, gu, ffield, tau_field, s);                            \
     }                                                                                                        \
     cudaError_t sums_##TAG(const StepArgs<Store<ST>::R>& a, double* partial, double* out, cudaStream_t s) {  \
         return launch_sums<L, ST>(a, partial, out, s);                                                       \

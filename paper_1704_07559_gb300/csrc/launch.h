@@ -22,7 +22,7 @@ constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in 
 #define LBM_DECLARE_ENTRY(TAG, R)                                                                         \
     cudaError_t step_##TAG(const StepArgs<R>& a, int closure, int formula, int force, cudaStream_t s);   \
     cudaError_t init_##TAG(const StepArgs<double>& a, int closure, const double* drho, const double* u, \
-                           const double* gu, const R* ffield, cudaStream_t s);                           \
+                           const double* gu, const R* ffield, R* tau_field, cudaStream_t s);             \
     cudaError_t sums_##TAG(const StepArgs<R>& a, double* partial, double* out, cudaStream_t s);
 
 LBM_DECLARE_ENTRY(d3q19_f64, double)

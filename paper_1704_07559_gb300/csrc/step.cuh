@@ -38,7 +38,7 @@
 
 namespace lbm {
 
-enum { CL_NEWTON = 0, CL_SMAG = 1, CL_POWERLAW = 2 };
+enum { CL_NEWTON = 0, CL_SMAG = 1, CL_POWERLAW = 2, CL_SMAG_LAGGED = 3, CL_SMAG_DEV = 4 };
 enum { F_YU = 0, F_CHAI = 1 };
 
 // ------------------------------------------------------------------------------------------
@@ -162,6 +162,7 @@ struct StepArgs {
     RS* tau_out;
     RS* drho_out;
     RS* u_out;
+    RS* tau_field;         // lagged closure: N stored taus, read and rewritten in place by each node
 };
 
 // ------------------------------------------------------------------------------------------
@@ -245,8 +246,8 @@ __host__ __device__ constexpr uint32_t mask_all_but_density() {
 }
 
 // Forward and backward transforms.  The generic form (any lattice) sums the nonzero entries of
-// each row of T over the opposite-pair sums and differences.  D3Q19 has a hand-factored form
-// that shares the axis / edge partial sums between rows; it computes the same linear maps.
+// each row of T over the opposite-pair sums and differences.  D3Q19 and D3Q15 have hand-factored forms
+// that share partial sums (axis / edge / corner butterflies) between rows; they compute the same maps.
 template <class L>
 struct Xf {
     // m[k] = (T f)_k for every k (m[0] = drho, m[3], m[5], m[7] = raw momentum)
@@ -371,6 +372,84 @@ struct Xf<D3Q19> {
                 out[16] = E9 + O9;
                 out[17] = E9 - O9;
             }
+        }
+    }
+};
+
+template <>
+struct Xf<D3Q15> {
+    // pair order: x (1,2), y (3,4), z (5,6), corners (7,14), (8,13), (9,12), (10,11); the four corner
+    // pairs are combined by two-level butterflies shared between rows
+    template <class R>
+    static __device__ __forceinline__ void forward(R f0, const R (&P)[7], const R (&D)[7], R (&m)[15]) {
+        const R a = P[3] + P[6], b = P[4] + P[5], c = P[3] - P[6], d = P[4] - P[5];
+        const R Sc = a + b, Sax = P[0] + (P[1] + P[2]);
+        const R u = D[3] + D[5], v = D[4] + D[6], w = D[3] - D[5], x = D[4] - D[6];
+        const R Cx = u - v, Cy = w + x, Cz = u + v;
+        m[0] = f0 + Sax + Sc;
+        m[1] = fma(R(-2.0f), f0, Sc - Sax);
+        m[2] = fma(R(16.0f), f0, fma(R(-4.0f), Sax, Sc));
+        m[3] = D[0] + Cx;
+        m[4] = fma(R(-4.0f), D[0], Cx);
+        m[5] = D[1] + Cy;
+        m[6] = fma(R(-4.0f), D[1], Cy);
+        m[7] = D[2] + Cz;
+        m[8] = fma(R(-4.0f), D[2], Cz);
+        m[9] = fma(R(3.0f), P[0], -Sax);
+        m[10] = P[1] - P[2];
+        m[11] = a - b;
+        m[12] = c + d;
+        m[13] = c - d;
+        m[14] = w - x;
+    }
+
+    // out_i = sum_k T_ki a_k for every non-conserved a_k (with CONS also a_3, a_5, a_7); other
+    // masks use the generic form
+    template <uint32_t USE, class R>
+    static __device__ __forceinline__ void backward(const R (&a)[15], R (&out)[15]) {
+        constexpr uint32_t NC = mask_nonconserved<D3Q15>();
+        if constexpr (USE != NC && USE != mask_all_but_density<D3Q15>()) {
+            back_transform<D3Q15, USE>(a, out);
+        } else {
+            constexpr bool CONS = (USE >> 3) & 1u;
+            out[0] = fma(R(16.0f), a[2], R(-2.0f) * a[1]);
+            // axis populations
+            const R B1 = fma(R(-4.0f), a[2], -a[1]);
+            const R Ex = fma(R(2.0f), a[9], B1), BC = B1 - a[9];
+            const R Ey = BC + a[10], Ez = BC - a[10];
+            R Ox, Oy, Oz, X = a[4], Y = a[6], Z = a[8];
+            if constexpr (CONS) {
+                Ox = fma(R(-4.0f), a[4], a[3]);
+                Oy = fma(R(-4.0f), a[6], a[5]);
+                Oz = fma(R(-4.0f), a[8], a[7]);
+                X += a[3];
+                Y += a[5];
+                Z += a[7];
+            } else {
+                Ox = R(-4.0f) * a[4];
+                Oy = R(-4.0f) * a[6];
+                Oz = R(-4.0f) * a[8];
+            }
+            out[1] = Ex + Ox;
+            out[2] = Ex - Ox;
+            out[3] = Ey + Oy;
+            out[4] = Ey - Oy;
+            out[5] = Ez + Oz;
+            out[6] = Ez - Oz;
+            // corner populations: even parts B2 +- a11 +- a12 +- a13, odd parts +-X +-Y +-Z +- a14
+            const R B2 = a[1] + a[2];
+            const R s = B2 + a[11], t = B2 - a[11], g = a[12] + a[13], h = a[12] - a[13];
+            const R U = Z + Y, V = Z - Y, p = X + a[14], r = a[14] - X;
+            const R E3 = s + g, E6 = s - g, E4 = t + h, E5 = t - h;
+            const R O3 = U + p, O4 = U - p, O5 = V - r, O6 = V + r;
+            out[7] = E3 + O3;
+            out[14] = E3 - O3;
+            out[8] = E4 + O4;
+            out[13] = E4 - O4;
+            out[9] = E5 + O5;
+            out[12] = E5 - O5;
+            out[10] = E6 + O6;
+            out[11] = E6 - O6;
         }
     }
 };
@@ -619,6 +698,23 @@ __device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const
 // ------------------------------------------------------------------------------------------
 // closure: solve tau with S = A + (1/tau) B
 
+// per-node fields of the compute type (one node, or the aligned pair of the packed form)
+template <class R, class RS>
+__device__ __forceinline__ R load_field(const RS* p) {
+    if constexpr (std::is_same<R, F2>::value)
+        return F2(*reinterpret_cast<const float2*>(p));
+    else
+        return *p;
+}
+template <class R, class RS>
+__device__ __forceinline__ void store_field(RS* p, R v) {
+    if constexpr (std::is_same<R, F2>::value)
+        *reinterpret_cast<float2*>(p) = v.v;
+    else
+        *p = v;
+}
+
+
 template <class L, class R>
 __device__ __forceinline__ R strain_dot(const R (&S)[L::NS], const R (&T)[L::NS]) {
     // S:T with the off-diagonal components counted twice
@@ -663,15 +759,57 @@ __device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepAr
     return tau;
 }
 
+// Deviatoric Smagorinsky, tau = tau0 + 3 Cs^2 |S_d(1/tau)|.  On these bases the rate-free part A is
+// isotropic and B is traceless, so S_d = s B and tau is the larger root of
+// tau^2 - tau0 tau - 3 Cs^2 |B| = 0, |B| = sqrt(2 B:B).
+template <class RS>
+__device__ __forceinline__ RS tau_deviatoric(RS qc, const StepArgs<RS>& a) {
+    const RS b = c_sqrt(RS(2) * qc);
+    return RS(0.5) * (a.tau0 + c_sqrt(fma(a.tau0, a.tau0, RS(4) * a.smag_c3 * b)));
+}
+
 // Returns tau, sets snu = 1/tau and S = A + snu B.  For the packed pair each node solves its own
-// fixed point.
+// fixed point.  The lagged closure collides with tau_prev, the tau stored at the (first) node
+// `node` (loaded by the caller together with the populations), and in a step (not a read-out)
+// stores tau0 + 3 Cs^2 |S| there for the next step.
 template <class L, class R, int CLOSURE, class RS>
 __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS], const StepArgs<RS>& a,
-                                       R (&S)[L::NS], R& snu) {
+                                       R (&S)[L::NS], R& snu, int node, R tau_prev = R(0.0f)) {
+    constexpr bool PAIR = std::is_same<R, F2>::value;
     if constexpr (CLOSURE == CL_NEWTON) {
         snu = R(a.s[L::NU0]);
         affine<L>(A, B, snu, S);
         return R(a.tau0);
+    } else if constexpr (CLOSURE == CL_SMAG_LAGGED) {
+        const R tau = tau_prev;
+        if constexpr (PAIR)
+            snu = F2(c_rcp(tau.lo()), c_rcp(tau.hi()));
+        else
+            snu = c_rcp(tau);
+        affine<L>(A, B, snu, S);
+        if (!a.readout) {
+            const R ss = strain_dot<L>(S, S);
+            R tn;
+            if constexpr (PAIR)
+                tn = F2(fma(a.smag_c3, c_sqrt(2.0f * ss.lo()), a.tau0), fma(a.smag_c3, c_sqrt(2.0f * ss.hi()), a.tau0));
+            else
+                tn = fma(a.smag_c3, c_sqrt(RS(2) * ss), a.tau0);
+            store_field(a.tau_field + node, tn);
+        }
+        return tau;
+    } else if constexpr (CLOSURE == CL_SMAG_DEV) {
+        const R qc = strain_dot<L>(B, B);
+        R tau;
+        if constexpr (PAIR) {
+            const float t0 = tau_deviatoric(qc.lo(), a), t1 = tau_deviatoric(qc.hi(), a);
+            tau = F2(t0, t1);
+            snu = F2(c_rcp(t0), c_rcp(t1));
+        } else {
+            tau = tau_deviatoric(qc, a);
+            snu = c_rcp(tau);
+        }
+        affine<L>(A, B, snu, S);
+        return tau;
     } else {
         const R qa = strain_dot<L>(A, A), qb2 = R(2.0f) * strain_dot<L>(A, B), qc = strain_dot<L>(B, B);
         R tau;
@@ -791,20 +929,15 @@ __device__ __forceinline__ void pull2(const StepArgs<float>& a, int x0, int y, i
 // ------------------------------------------------------------------------------------------
 // the fused step
 
-template <class R, class RS>
-__device__ __forceinline__ R load_field(const RS* p) {
-    if constexpr (std::is_same<R, F2>::value)
-        return F2(*reinterpret_cast<const float2*>(p));
-    else
-        return *p;
-}
-template <class R, class RS>
-__device__ __forceinline__ void store_field(RS* p, R v) {
-    if constexpr (std::is_same<R, F2>::value)
-        *reinterpret_cast<float2*>(p) = v.v;
-    else
-        *p = v;
-}
+// Programmatic dependent launch.  A step launched with the programmatic-serialization attribute
+// may become resident while the previous kernel of the stream is finishing; griddepcontrol.wait
+// returns once that kernel has completed and its memory operations are visible, so it precedes
+// every load.  launch_dependents lets the next such step be scheduled as soon as every block of
+// this one has issued it; issued at block start, that happens once the last blocks are resident,
+// so waiting blocks of the next step only take slots freed by this one.  Launched without the
+// attribute, both instructions have no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Everything of a step after the pull, for the node(s) starting at `node`: moments, strain rate
 // by the chosen route, closure, relaxation, force, and either the store of f* or (readout) the
@@ -831,6 +964,9 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
             sfor<L::D>([&](auto d) { F[d] = R(a.F[d]); });
         }
     }
+    // the lagged closure's stored tau, loaded next to the populations so its latency overlaps theirs
+    R tau_prev = R(0.0f);
+    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_field<R>(a.tau_field + node);
     const R ir0 = R(a.inv_rho0);
     R drho, j[3] = {R(0.0f), R(0.0f), R(0.0f)}, u[3] = {R(0.0f), R(0.0f), R(0.0f)};
     R S[NS], tau, snu;
@@ -882,7 +1018,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
         }
         R A[NS], B[NS];
         Eq<L>::yu_split(mn, R(a.s[1] * RS(Eq<L>::YU_A)) * ir0, ir0, A, B);
-        tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
+        tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu, node, tau_prev);
         if (a.readout) goto readout;
         sfor<Q>([&](auto k) {
             if constexpr (L::viscous(CV(k))) {
@@ -964,7 +1100,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
                 A[c] = kS * Nf[c];
                 B[c] = kS * Nv[c];
             }
-            tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu);
+            tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu, node, tau_prev);
             if (a.readout) goto readout;
             sfor<Q>([&](auto i) { out[i] = fma(snu, Ov[i], Om[i]); });
         }
@@ -1003,6 +1139,8 @@ template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
 __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
     using RS = typename Store<ST>::R;
     using R = std::conditional_t<VW == 2, F2, RS>;
+    pdl_wait();     // the previous step's stores are complete and visible from here on
+    pdl_release();  // every block has started: the next step may be scheduled into freed slots
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -1021,7 +1159,8 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
 template <class L, class ST>
 __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int closure, const double* __restrict__ drho,
                                               const double* __restrict__ u, const double* __restrict__ gu,
-                                              const typename Store<ST>::R* __restrict__ ffield) {
+                                              const typename Store<ST>::R* __restrict__ ffield,
+                                              typename Store<ST>::R* __restrict__ tau_field) {
     using R = typename Store<ST>::R;
     constexpr int Q = L::Q, D = L::D;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1040,30 +1179,35 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
     double mn[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) mn[k] = 0.0;
-    if (gu) {
-        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    // the closure's tau at the prescribed gradient (explicit, since S is given); the lagged
+    // closure stores it as the tau of the first step
+    double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (gu)
         for (int p = 0; p < D; ++p)
             for (int q = 0; q < D; ++q) G[p][q] = r0 * gu[(p * D + q) * N + node];
-        double snu = a.s[L::NU0];
-        if (closure != CL_NEWTON) {
-            double ss;
-            if (D == 3)
-                ss = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
-                     0.5 * ((G[0][1] + G[1][0]) * (G[0][1] + G[1][0]) + (G[1][2] + G[2][1]) * (G[1][2] + G[2][1]) +
-                            (G[0][2] + G[2][0]) * (G[0][2] + G[2][0]));
-            else
-                ss = G[0][0] * G[0][0] + G[1][1] * G[1][1] + 0.5 * (G[0][1] + G[1][0]) * (G[0][1] + G[1][0]);
-            const double gnorm = sqrt(2.0 * ss) * ir0;
-            double tau;
-            if (closure == CL_SMAG) {
-                tau = a.tau0 + a.smag_c3 * gnorm;
-            } else {
-                tau = 0.5 + a.pl_k3 * pow(gnorm, a.pl_nm1);
-                if (!(tau >= a.pl_tau_min)) tau = a.pl_tau_min;
-                if (tau > a.pl_tau_max) tau = a.pl_tau_max;
-            }
-            snu = 1.0 / tau;
+    double tau_i = a.tau0;
+    if (closure != CL_NEWTON) {
+        double ss, tr = 0.0;
+        if (closure == CL_SMAG_DEV) tr = (G[0][0] + G[1][1] + G[2][2]) / D;  // traceless part only
+        const double e0 = G[0][0] - tr, e1 = G[1][1] - tr, e2 = D == 3 ? G[2][2] - tr : 0.0;
+        if (D == 3)
+            ss = e0 * e0 + e1 * e1 + e2 * e2 +
+                 0.5 * ((G[0][1] + G[1][0]) * (G[0][1] + G[1][0]) + (G[1][2] + G[2][1]) * (G[1][2] + G[2][1]) +
+                        (G[0][2] + G[2][0]) * (G[0][2] + G[2][0]));
+        else
+            ss = e0 * e0 + e1 * e1 + 0.5 * (G[0][1] + G[1][0]) * (G[0][1] + G[1][0]);
+        const double gnorm = sqrt(2.0 * ss) * ir0;
+        if (closure == CL_POWERLAW) {
+            tau_i = 0.5 + a.pl_k3 * pow(gnorm, a.pl_nm1);
+            if (!(tau_i >= a.pl_tau_min)) tau_i = a.pl_tau_min;
+            if (tau_i > a.pl_tau_max) tau_i = a.pl_tau_max;
+        } else {
+            tau_i = a.tau0 + a.smag_c3 * gnorm;
         }
+    }
+    if (tau_field) tau_field[node] = R(tau_i);
+    if (gu) {
+        const double snu = closure == CL_NEWTON ? double(a.s[L::NU0]) : 1.0 / tau_i;
         const double divj = G[0][0] + G[1][1] + G[2][2];
         if constexpr (Q == 19) {
             mn[1] = -38.0 / (3.0 * a.s[1]) * divj;

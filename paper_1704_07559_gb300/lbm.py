@@ -19,13 +19,13 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 D2Q9, D3Q15, D3Q19 = 9, 15, 19
 PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2, "bf16s": 3}
-CLOSURE = {"newton": 0, "smag": 1, "powerlaw": 2}
+CLOSURE = {"newton": 0, "smag": 1, "powerlaw": 2, "smag_lagged": 3, "smag_dev": 4}
 FORMULA = {"yu": 0, "chai": 1}
 BC = {"periodic": 0, "wall": 1, "lid": 2}
 STORAGE_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_STATE"}
-API = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_layout", "lbm_bind", "lbm_init", "lbm_step",
-       "lbm_strain_rate", "lbm_macroscopic", "lbm_sums", "lbm_get_state", "lbm_set_state", "lbm_last_error",
+API = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_layout", "lbm_bind", "lbm_bind_tau", "lbm_init",
+       "lbm_step", "lbm_strain_rate", "lbm_macroscopic", "lbm_sums", "lbm_get_state", "lbm_set_state", "lbm_last_error",
        "lbm_sums_noalloc", "lbm_adjoint_workspace", "lbm_adjoint"]
 
 
@@ -76,6 +76,7 @@ def lib():
     L.lbm_destroy.argtypes = [vp]
     L.lbm_layout.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64), ip]
     L.lbm_bind.argtypes = [vp, vp, vp, vp, vp]
+    L.lbm_bind_tau.argtypes = [vp, vp]
     L.lbm_init.argtypes = [vp, vp, vp, vp]
     L.lbm_step.argtypes = [vp, ctypes.c_int]
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -171,6 +172,11 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._check(L.lbm_bind(ctx, _ptr(self.f_a), _ptr(self.f_b), _ptr(self.force_field),
                                ctypes.c_void_p(self.stream.cuda_stream)))
+        # the lagged closure's per-node tau (state carried from step to step)
+        self.tau = None
+        if p.closure == CLOSURE["smag_lagged"]:
+            self.tau = torch.empty(self.shape, dtype=self.compute_dtype, device=self.device)
+            self._check(L.lbm_bind_tau(ctx, _ptr(self.tau)))
 
     # -- plumbing --------------------------------------------------------------------------
     def _check(self, rc):

@@ -28,7 +28,8 @@ TOL = {"fp64": dict(S=1e-12, f=1e-12), "fp32": dict(S=1e-5, f=2e-6),
        "fp16s": dict(S=1e-5, f=2e-6, eps=2.0 ** -11, abs=2.0 ** -24),
        "bf16s": dict(S=1e-5, f=2e-6, eps=2.0 ** -8)}
 BCN = {"periodic": O.PERIODIC, "wall": O.WALL, "lid": O.LID}
-CL = {"newton": O.NEWTON, "smag": O.SMAG, "powerlaw": O.POWERLAW}
+CL = {"newton": O.NEWTON, "smag": O.SMAG, "powerlaw": O.POWERLAW, "smag_lagged": O.SMAG_LAGGED,
+      "smag_dev": O.SMAG_DEV}
 
 
 def sample_nodes(dims, n_random, seed, d):
@@ -88,6 +89,8 @@ def check_sampled(lat, rates, precision, closure, formula, bc, nodes, force=None
     fin = lat.get_state()
     patches = [patch(fin, p, dims, bc, d) for p in nodes]
     del fin
+    lagged = lat.tau is not None  # the lagged closure reads each node's stored tau
+    tau_in = at_nodes(lat.tau, nodes) if lagged else None
     reads = {}
     for fm in formulas:
         S, tau = lat.strain_rate(fm, with_tau=True)
@@ -95,6 +98,7 @@ def check_sampled(lat, rates, precision, closure, formula, bc, nodes, force=None
         del S, tau
     lat.step(1)
     fout = at_nodes(lat.get_state(), nodes)
+    tau_next = at_nodes(lat.tau, nodes) if lagged else None
     lid_u = [[0.0, 0.0, 0.0] for _ in range(6)]
     for fc, v in (lid or {}).items():
         lid_u[fc] = list(v)
@@ -106,6 +110,7 @@ def check_sampled(lat, rates, precision, closure, formula, bc, nodes, force=None
                              pl_tol=1e-14 if precision == "fp64" else 1e-7)
 
     fo = np.zeros((q, len(nodes)))
+    tn_o = np.zeros(len(nodes))
     So = {fm: np.zeros((lat.ns, len(nodes))) for fm in formulas}
     to = {fm: np.zeros(len(nodes)) for fm in formulas}
     for k, (node, (sub, c, kinds)) in enumerate(zip(nodes, patches)):
@@ -114,32 +119,35 @@ def check_sampled(lat, rates, precision, closure, formula, bc, nodes, force=None
         else:
             F = None if force is None else np.array(force, dtype=np.float64)
         pdims = (sub.shape[3], sub.shape[2], sub.shape[1])
+        tp = np.full(sub.shape[1:], tau_in[k]) if lagged else None
         for fm in formulas:
             G = O.Grid(params(kinds, fm), *pdims)
-            f1, S1, t1, _, _ = G.node(sub, c[0], c[1], c[2], force=F)
+            f1, S1, t1, _, _, tn1 = G.node(sub, c[0], c[1], c[2], force=F, tau=tp, with_next=True)
             So[fm][:, k], to[fm][k] = S1, t1
             if fm == formula:
-                fo[:, k] = f1
+                fo[:, k], tn_o[k] = f1, tn1
     for fm in formulas:
         assert relerr(reads[fm][0], So[fm]) <= t["S"], (fm, relerr(reads[fm][0], So[fm]))
         assert relerr(reads[fm][1], to[fm]) <= t["S"], (fm, relerr(reads[fm][1], to[fm]))
     bound = t.get("eps", 0.0) * np.abs(fo) + t["f"] * np.abs(fo).max() + t.get("abs", 0.0)
     assert np.all(np.abs(fout - fo) <= bound), relerr(fout, fo)
+    if lagged:
+        assert relerr(tau_next, tn_o) <= t["S"]
     return So[formula]
 
 
-@pytest.mark.parametrize("lattice,precision,formula", [(19, "fp32", "yu"), (19, "fp32", "chai"),
-                                                       (19, "fp16s", "yu"), (19, "bf16s", "chai"),
-                                                       (19, "fp64", "yu"), (15, "fp32", "yu"),
-                                                       (15, "fp32", "chai")])
-def test_channel_256x128x128_sampled(lattice, precision, formula):
-    """The headline channel (walls at y, g_x = 1e-6, Smagorinsky) after 10 steps."""
-    lat = bench.make_lattice(precision, formula, lattice=lattice)
+@pytest.mark.parametrize("lattice,precision,formula,closure", [
+    (19, "fp32", "yu", "smag"), (19, "fp32", "chai", "smag"), (19, "fp16s", "yu", "smag"),
+    (19, "bf16s", "chai", "smag"), (19, "fp64", "yu", "smag"), (15, "fp32", "yu", "smag"), (15, "fp32", "chai", "smag"),
+    (19, "fp32", "yu", "smag_lagged"), (19, "fp32", "chai", "smag_dev")])
+def test_channel_256x128x128_sampled(lattice, precision, formula, closure):
+    """The headline channel (walls at y, g_x = 1e-6, Smagorinsky or a variant) after 10 steps."""
+    lat = bench.make_lattice(precision, formula, lattice=lattice, closure=closure)
     lat.step(10)
     nodes = sample_nodes((lat.nx, lat.ny, lat.nz), 120, seed=lattice + len(precision), d=3)
     nodes += [(x, y, 64) for x in (3, 200) for y in (0, 1, 126, 127)]  # wall rows
     rates = bench.RATES if lattice == 19 else bench.RATES15
-    S = check_sampled(lat, rates, precision, "smag", formula, bench.BC, sorted(set(nodes)), force=[bench.G, 0, 0],
+    S = check_sampled(lat, rates, precision, closure, formula, bench.BC, sorted(set(nodes)), force=[bench.G, 0, 0],
                       smag_cs=bench.CS)
     assert np.abs(S).max() > 1e-4  # the sample carries a real strain rate
     lat.close()

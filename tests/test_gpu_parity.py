@@ -66,8 +66,9 @@ class Case:
         lid_u = [[0.0, 0.0, 0.0] for _ in range(6)]
         for f, v in self.lid.items():
             lid_u[f] = list(v)
-        self.p = O.make_params(q, rates(q, tau), closure={"newton": O.NEWTON, "smag": O.SMAG,
-                                                          "powerlaw": O.POWERLAW}[closure],
+        self.p = O.make_params(q, rates(q, tau), closure={"newton": O.NEWTON, "smag": O.SMAG, "powerlaw": O.POWERLAW,
+                                                          "smag_lagged": O.SMAG_LAGGED,
+                                                          "smag_dev": O.SMAG_DEV}[closure],
                                formula=O.YU if formula == "yu" else O.CHAI, bc=[BCN[b] for b in self.bc],
                                lid_u=lid_u, smag_cs=smag_cs, pl_n=pl[0], pl_k=pl[1],
                                pl_tol=1e-14 if precision == "fp64" else 1e-7)
@@ -86,22 +87,29 @@ class Case:
     def check_init(self):
         self.lat.init(self.drho, self.u, self.g)
         fg = f64(self.lat.get_state())
-        fo = self.G.init(self.drho, self.u, self.g, force=self.oforce)
+        fo, to = self.G.init(self.drho, self.u, self.g, force=self.oforce, with_tau=True)
         t = TOL[self.precision]
         bound = t.get("eps", 0.0) * np.abs(fo) + t["f"] * np.abs(fo).max() + t.get("abs", 0.0)
         assert np.all(np.abs(fg - fo) <= bound), relerr(fg, fo)
+        if self.lat.tau is not None:  # the lagged closure's first stored tau
+            assert relerr(f64(self.lat.tau), to) <= t["m"]
         return fg
+
+    @property
+    def tau_in(self):
+        return None if self.lat.tau is None else f64(self.lat.tau)
 
     def check_step(self, formulas=("yu", "chai")):
         """Read-outs of the current state, then one step, each against the oracle."""
         t = TOL[self.precision]
         fin = f64(self.lat.get_state())
-        fo, out = self.G.step(fin, force=self.oforce, want=("S", "tau", "drho", "u"))
+        tin = self.tau_in
+        fo, out = self.G.step(fin, force=self.oforce, want=("S", "tau", "drho", "u", "tau_next"), tau=tin)
         for fm in formulas:
             S, tau = self.lat.strain_rate(fm, with_tau=True)
             p_saved = self.p.formula
             self.p.formula = O.YU if fm == "yu" else O.CHAI
-            ro = self.G.readout(fin, force=self.oforce)
+            ro = self.G.readout(fin, force=self.oforce, tau=tin)
             self.p.formula = p_saved
             assert relerr(f64(S), ro["S"]) <= t["S"], (fm, relerr(f64(S), ro["S"]))
             assert relerr(f64(tau), ro["tau"]) <= t["S"], (fm, relerr(f64(tau), ro["tau"]))
@@ -112,6 +120,8 @@ class Case:
         fg = f64(self.lat.get_state())
         bound = t.get("eps", 0.0) * np.abs(fo) + t["f"] * np.abs(fo).max() + t.get("abs", 0.0)
         assert np.all(np.abs(fg - fo) <= bound), relerr(fg, fo)
+        if self.lat.tau is not None:  # the tau stored for the next step
+            assert relerr(f64(self.lat.tau), out["tau_next"]) <= t["S"]
         return fg
 
     def check_sums(self):
@@ -158,6 +168,14 @@ CASES = [
                                                     force=[1e-5, 0, 0], tau=0.51)),
     (15, (33, 17, 5), "fp32", "powerlaw", "chai", dict(force_field=True, pl=(0.7, 0.01), tau=0.7)),
     (15, (11, 10, 9), "fp32", "newton", "yu", dict(bc=["wall"] * 4 + ["periodic"] * 2)),
+    (19, (130, 9, 6), "fp64", "smag_lagged", "yu", dict(bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+                                                         force=[1e-5, 0, 0], tau=0.51)),
+    (19, (130, 9, 6), "fp32", "smag_lagged", "chai", dict(force_field=True, tau=0.51)),
+    (19, (150, 7, 5), "fp64", "smag_dev", "chai", dict(force=[1e-5, -2e-5, 3e-6], tau=0.51)),
+    (19, (130, 9, 6), "fp32", "smag_dev", "yu", dict(bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+                                                      force=[1e-5, 0, 0], tau=0.51)),
+    (15, (33, 17, 5), "fp32", "smag_lagged", "yu", dict(tau=0.51)),
+    (9, (97, 40, 1), "fp32", "smag_dev", "chai", dict(bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)}, tau=0.51)),
 ]
 
 
@@ -226,3 +244,39 @@ def test_errors_are_reported_not_raised_as_faults():
     with pytest.raises(lbm.LBMError):
         lat2.strain_rate("yu")
     lat2.strain_rate("chai")
+
+
+def test_lagged_closure_needs_its_tau_field():
+    """Through the raw C ABI: with the lagged closure and no tau field bound, init, step and
+    read-outs report LBM_ERR_STATE (no kernel runs); after lbm_bind_tau they succeed."""
+    import ctypes
+
+    L = lbm.lib()
+    p = lbm.default_params()
+    p.closure = 3
+    p.smag_cs = 0.17
+    r = rates(19, 0.6)
+    ctx = ctypes.c_void_p()
+    assert L.lbm_create(ctypes.byref(ctx), 19, 8, 8, 8, (ctypes.c_double * 19)(*r), None, ctypes.byref(p)) == 0
+    stride = ctypes.c_int64()
+    L.lbm_layout(ctx, None, ctypes.byref(stride), None)
+    fa = torch.zeros((19, stride.value), dtype=torch.float32, device="cuda")
+    fb = torch.zeros_like(fa)
+    s = torch.cuda.current_stream()
+    assert L.lbm_bind(ctx, ctypes.c_void_p(fa.data_ptr()), ctypes.c_void_p(fb.data_ptr()), None,
+                      ctypes.c_void_p(s.cuda_stream)) == 0
+    drho = torch.zeros(512, dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * 512, dtype=torch.float64, device="cuda")
+    vp = ctypes.c_void_p
+    assert L.lbm_init(ctx, vp(drho.data_ptr()), vp(u.data_ptr()), None) == -5
+    assert L.lbm_step(ctx, 1) == -5
+    S = torch.empty(6 * 512, dtype=torch.float32, device="cuda")
+    assert L.lbm_strain_rate(ctx, 0, vp(S.data_ptr()), None) == -5
+    assert L.lbm_bind_tau(ctx, None) == -1
+    tau = torch.empty(512, dtype=torch.float32, device="cuda")
+    assert L.lbm_bind_tau(ctx, vp(tau.data_ptr())) == 0
+    assert L.lbm_init(ctx, vp(drho.data_ptr()), vp(u.data_ptr()), None) == 0
+    assert L.lbm_step(ctx, 2) == 0
+    torch.cuda.synchronize()
+    assert torch.all(tau == torch.tensor(1 / r[9], dtype=torch.float32, device="cuda"))  # fluid at rest
+    L.lbm_destroy(ctx)

@@ -79,6 +79,10 @@ def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
     dict(lattice=15, rates=D15[:7] + [0.3] + D15[8:]),                  # D3Q15 conserved j_z rate
     dict(lattice=15, rates=D15[:12] + [1.5] + D15[13:]),                # D3Q15 split viscous rates, Yu
     dict(lattice=15, dims=(8, 8, 0)),
+    dict(mutate=lambda p: setattr(p, "closure", 5)),
+    dict(mutate=lambda p: (setattr(p, "precision", 2), setattr(p, "closure", 3))),  # 16-bit: lagged
+    dict(mutate=lambda p: (setattr(p, "precision", 3), setattr(p, "closure", 4))),  # 16-bit: deviatoric
+    dict(rates=D3[:13] + [1.2] + D3[14:], mutate=lambda p: (setattr(p, "formula", 1), setattr(p, "closure", 3))),
 ])
 def test_create_rejects_bad_arguments(L, case):
     rc, ctx = create(L, **case)
@@ -106,5 +110,6 @@ def test_d3q15_host_checks_pass(L):
 
 def test_null_context_calls_fail_cleanly(L):
     assert L.lbm_step(None, 1) == -1
+    assert L.lbm_bind_tau(None, None) == -1
     assert L.lbm_destroy(None) == 0
     assert L.lbm_layout(None, None, None, None) == -1
