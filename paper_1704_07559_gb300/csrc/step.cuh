@@ -759,6 +759,24 @@ __device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepAr
     return tau;
 }
 
+// A per-node field value loaded with an asm volatile ld (its issue point stays where it is written)
+template <class R, class RS>
+__device__ __forceinline__ R load_early(const RS* p) {
+    if constexpr (std::is_same<R, F2>::value) {
+        float2 v;
+        asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+        return F2(v);
+    } else if constexpr (std::is_same<RS, double>::value) {
+        double v;
+        asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    } else {
+        float v;
+        asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
+}
+
 // Deviatoric Smagorinsky, tau = tau0 + 3 Cs^2 |S_d(1/tau)|.  On these bases the rate-free part A is
 // isotropic and B is traceless, so S_d = s B and tau is the larger root of
 // tau^2 - tau0 tau - 3 Cs^2 |B| = 0, |B| = sqrt(2 B:B).
@@ -965,8 +983,9 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
         }
     }
     // the lagged closure's stored tau, loaded next to the populations so its latency overlaps theirs
+    // (an asm volatile load keeps it there instead of next to its use after the moment arithmetic)
     R tau_prev = R(0.0f);
-    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_field<R>(a.tau_field + node);
+    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_early<R>(a.tau_field + node);
     const R ir0 = R(a.inv_rho0);
     R drho, j[3] = {R(0.0f), R(0.0f), R(0.0f)}, u[3] = {R(0.0f), R(0.0f), R(0.0f)};
     R S[NS], tau, snu;
@@ -1135,8 +1154,14 @@ readout:
     }
 }
 
+// Minimum resident blocks per SM requested for the packed two-node form (bounds its registers:
+// 4 blocks of 128 threads leave 128 registers a thread, 5 leave 102, 6 leave 85).
+#ifndef LBM_VW2_MIN_BLOCKS
+#define LBM_VW2_MIN_BLOCKS 1
+#endif
+
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
-__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
+__global__ void __launch_bounds__(128, (VW == 2 ? LBM_VW2_MIN_BLOCKS : 1)) k_step(const StepArgs<typename Store<ST>::R> a) {
     using RS = typename Store<ST>::R;
     using R = std::conditional_t<VW == 2, F2, RS>;
     pdl_wait();     // the previous step's stores are complete and visible from here on
