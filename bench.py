@@ -198,29 +198,108 @@ def time_e2e(lat, steps):
     return dt / steps, h2d, 8 * (1 + lat.d)
 
 
-def cpu_baseline(seconds_budget=15.0):
-    """The FP64 oracle on the host cores, on a 64 x 32 x 32 sub-box of the same channel
-    (same rates, closure, force and walls), Yu route, as many steps as fit the budget."""
+def _oracle_channel_box(nx, ny, nz):
     import oracle as O
     from paper_1704_07559_gb300 import inputs as I
 
-    nx, ny, nz = 64, 32, 32
     p = O.make_params(19, RATES, closure=O.SMAG, smag_cs=CS, formula=O.YU,
                       bc=[O.PERIODIC, O.PERIODIC, O.WALL, O.WALL, O.PERIODIC, O.PERIODIC])
     Gr = O.Grid(p, nx, ny, nz)
     drho, u = I.channel_profile(nx, ny, nz, u_centre=0.1, noise=0.01, seed=2)
     F = np.array([G, 0.0, 0.0])
-    f = Gr.init(drho, u, force=F)
+    return Gr, Gr.init(drho, u, force=F), F
+
+
+def _oracle_replica(job):
+    """One host process: `steps` oracle steps on its own copy of a channel sub-box; returns
+    (node updates, seconds)."""
+    (nx, ny, nz), steps = job
+    Gr, f, F = _oracle_channel_box(nx, ny, nz)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f, _ = Gr.step(f, force=F)
+    return Gr.N * steps, time.perf_counter() - t0
+
+
+def alu_peaks():
+    """Measured FP32 and FP64 FMA throughput of this GPU (TFLOP/s, 2 flops per FMA), from the
+    benchmark's probe library: the arithmetic ceilings beside the HBM roofline."""
+    import ctypes
+
+    from paper_1704_07559_gb300 import build
+
+    lib = ctypes.CDLL(build.build_probe())
+    lib.fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name, fp64 in (("fp32_fma_tflops", 0), ("fp64_fma_tflops", 1)):
+        v = ctypes.c_double()
+        out[name] = round(v.value, 3) if lib.fma_peak(fp64, ctypes.byref(v)) == 0 else None
+    return out
+
+
+def host_cpu():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def cpu_baseline(seconds_budget=8.0):
+    """The FP64 oracle as it stands, on the host cores: one thread on a 64 x 32 x 32 sub-box of
+    the channel (same rates, closure, force and walls, Yu route); then one spawned process per
+    host core, each stepping its own copy of a 64^3 sub-box (the value reported: total node
+    updates / wall time); and one thread on the 512^2 D2Q9 power-law cavity (Chai route)."""
+    import multiprocessing as mp
+
+    import oracle as O
+
+    O.lib()  # built once before the workers start
+    nx, ny, nz = 64, 32, 32
+    Gr, f, F = _oracle_channel_box(nx, ny, nz)
     t0 = time.perf_counter()
     steps = 0
-    while True:
+    while time.perf_counter() - t0 < seconds_budget and steps < 200:
         f, _ = Gr.step(f, force=F)
         steps += 1
-        if time.perf_counter() - t0 > seconds_budget or steps >= 200:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": round(nx * ny * nz * steps / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%dx%dx%d sub-box of the channel, %d steps, FP64, Yu route, single thread" % (nx, ny, nz, steps)}
+    single = nx * ny * nz * steps / (time.perf_counter() - t0) / 1e6
+    cores = os.cpu_count() or 1
+    n64 = 64 ** 3
+    per = max(1, int(single * 1e6 * seconds_budget / n64))  # steps per replica for ~budget seconds
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_replica, [((64, 64, 64), per)] * cores)
+    wall = time.perf_counter() - t0
+    allcore = sum(r[0] for r in res) / wall / 1e6
+    # D2Q9 512^2 lid-driven power-law cavity (n = 0.5), one thread
+    L2, U = 512, 0.05
+    tau_ref = 0.5 + 3 * U * L2 / 1000.0
+    p9 = O.make_params(9, [0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / tau_ref, 1 / tau_ref], closure=O.POWERLAW,
+                       formula=O.CHAI, pl_n=0.5, pl_k=U ** 1.5 * L2 ** 0.5 / 1000.0,
+                       bc=[O.WALL, O.WALL, O.WALL, O.LID, O.PERIODIC, O.PERIODIC],
+                       lid_u=[[0, 0, 0]] * 3 + [[U, 0, 0]] + [[0, 0, 0]] * 2)
+    G9 = O.Grid(p9, L2, L2, 1)
+    f9 = G9.init(np.zeros((1, L2, L2)), np.zeros((2, 1, L2, L2)))
+    t0 = time.perf_counter()
+    s9 = 0
+    while time.perf_counter() - t0 < seconds_budget / 2 and s9 < 50:
+        f9, _ = G9.step(f9)
+        s9 += 1
+    d2q9 = L2 * L2 * s9 / (time.perf_counter() - t0) / 1e6
+    return {"value": round(allcore, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle, Yu route, channel rates/closure/force/walls: %d processes (one per host core), "
+                      "each %d steps of its own 64^3 sub-box" % (cores, per),
+            "single_thread": {"value": round(single, 4), "unit": "MLUPS",
+                              "sample": "%dx%dx%d sub-box of the channel, %d steps, one thread" % (nx, ny, nz, steps)},
+            "d2q9_512_cavity": {"value": round(d2q9, 4), "unit": "MLUPS",
+                                "sample": "512^2 power-law (n = 0.5) lid cavity, Chai route, %d steps, one thread" % s9},
+            "host_cpu": host_cpu()}
 
 
 def run_ours(args):
@@ -299,6 +378,7 @@ def run_ours(args):
         e2e_s, h2d, d2h = time_e2e(lat, max(3, min(args.steps, 50)))
         out["e2e"] = {"value": round(world * N / e2e_s / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h}
+        out["alu_peaks"] = alu_peaks()
         if not args.no_variants:
             out["variants"] = variants(args, hbm)
         if world == 1:

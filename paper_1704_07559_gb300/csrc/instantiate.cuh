@@ -52,26 +52,11 @@ cudaError_t launch_async(const StepArgs<typename Store<ST>::R>& a, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <class L, class ST, int C, int F, bool FO>
-cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
-    if constexpr (float_compute<ST>() && LBM_STEP_FORM != 0) {
-        if (LBM_STEP_FORM == 5 && !a.readout && a.nx % 2 == 0) {
-            dim3 g, b;
-            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
-            k_step<L, ST, C, F, FO, 2><<<g, b, 0, s>>>(a);
-            return cudaGetLastError();
-        }
-        if (LBM_STEP_FORM != 5 && !a.readout) {
-            constexpr bool PF = LBM_STEP_FORM >= 3;
-            constexpr bool PAIRS = LBM_STEP_FORM == 2 || LBM_STEP_FORM == 4;
-            if (PAIRS && a.nx % 2 == 0) return launch_async<L, ST, C, F, FO, 2, PF>(a, s);
-            return launch_async<L, ST, C, F, FO, 1, PF>(a, s);
-        }
-    }
-    dim3 g, b;
-    lattice_grid(a.nx, a.ny, a.nz, &g, &b);
-    // programmatic dependent launch: consecutive steps overlap launch and block scheduling with
-    // the previous step's tail (k_step waits for the previous kernel before its first load)
+// Programmatic dependent launch of a step kernel: consecutive steps overlap launch and block
+// scheduling with the previous step's tail (the kernel waits for the previous one before its
+// first load).
+template <class K, class A>
+cudaError_t launch_pdl(K kernel, dim3 g, dim3 b, cudaStream_t s, const A& a) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = g;
     cfg.blockDim = b;
@@ -82,7 +67,27 @@ cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step<L, ST, C, F, FO, 1>, a);
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+template <class L, class ST, int C, int F, bool FO>
+cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
+    if constexpr (float_compute<ST>() && LBM_STEP_FORM != 0) {
+        if (LBM_STEP_FORM == 5 && !a.readout && a.nx % 2 == 0) {
+            dim3 g, b;
+            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
+            return launch_pdl(k_step_pair<L, ST, C, F, FO>, g, b, s, a);
+        }
+        if (LBM_STEP_FORM != 5 && !a.readout) {
+            constexpr bool PF = LBM_STEP_FORM >= 3;
+            constexpr bool PAIRS = LBM_STEP_FORM == 2 || LBM_STEP_FORM == 4;
+            if (PAIRS && a.nx % 2 == 0) return launch_async<L, ST, C, F, FO, 2, PF>(a, s);
+            return launch_async<L, ST, C, F, FO, 1, PF>(a, s);
+        }
+    }
+    dim3 g, b;
+    lattice_grid(a.nx, a.ny, a.nz, &g, &b);
+    return launch_pdl(k_step<L, ST, C, F, FO, 1>, g, b, s, a);
 }
 
 template <class L, class ST, int C, int F>

@@ -1154,14 +1154,8 @@ readout:
     }
 }
 
-// Minimum resident blocks per SM requested for the packed two-node form (bounds its registers:
-// 4 blocks of 128 threads leave 128 registers a thread, 5 leave 102, 6 leave 85).
-#ifndef LBM_VW2_MIN_BLOCKS
-#define LBM_VW2_MIN_BLOCKS 1
-#endif
-
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
-__global__ void __launch_bounds__(128, (VW == 2 ? LBM_VW2_MIN_BLOCKS : 1)) k_step(const StepArgs<typename Store<ST>::R> a) {
+__device__ __forceinline__ void step_nodes(const StepArgs<typename Store<ST>::R>& a) {
     using RS = typename Store<ST>::R;
     using R = std::conditional_t<VW == 2, F2, RS>;
     pdl_wait();     // the previous step's stores are complete and visible from here on
@@ -1176,6 +1170,26 @@ __global__ void __launch_bounds__(128, (VW == 2 ? LBM_VW2_MIN_BLOCKS : 1)) k_ste
     else
         pull<L, ST>(a, x, y, z, f);
     step_body<L, ST, CLOSURE, FORMULA, FORCE, VW>(a, f, (z * a.ny + y) * a.nx + x);
+}
+
+// One node per thread (the dispatched form).  The bound is written as the thread count alone:
+// naming a minimum of one block changes ptxas's register allocation (more registers, fewer
+// resident blocks).
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
+__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
+    step_nodes<L, ST, CLOSURE, FORMULA, FORCE, VW>(a);
+}
+
+// Two x-adjacent nodes per thread in packed FP32 pairs, with a minimum number of resident blocks
+// per SM that bounds its registers (3 blocks of 128 threads leave 170 registers a thread, 4 leave
+// 128, 5 leave 102).
+#ifndef LBM_VW2_MIN_BLOCKS
+#define LBM_VW2_MIN_BLOCKS 3
+#endif
+
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__global__ void __launch_bounds__(128, LBM_VW2_MIN_BLOCKS) k_step_pair(const StepArgs<typename Store<ST>::R> a) {
+    step_nodes<L, ST, CLOSURE, FORMULA, FORCE, 2>(a);
 }
 
 // ------------------------------------------------------------------------------------------
