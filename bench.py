@@ -221,6 +221,22 @@ def _oracle_replica(job):
     return Gr.N * steps, time.perf_counter() - t0
 
 
+def job_rate(ms_local, updates_local, dist=None, device="cpu"):
+    """Whole-job rate of N replicas: the slowest rank's time of the timed region (max over ranks)
+    and all ranks' node updates / that time, in MLUPS.  dist: torch.distributed (initialised) or
+    None for one process; every rank does the same number of updates."""
+    import torch
+
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_local = float(t.item())
+        dist.barrier()
+    return ms_local, world * updates_local / (ms_local * 1e-3) / 1e6
+
+
 def alu_peaks():
     """Measured FP32 and FP64 FMA throughput of this GPU (TFLOP/s, 2 flops per FMA), from the
     benchmark's probe library: the arithmetic ceilings beside the HBM roofline."""
@@ -339,18 +355,16 @@ def run_ours(args):
     with ClockSampler(gpu_index) as clk:
         ms = time_steps(lat, args.steps, 0)
         torch.cuda.synchronize()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    local_ms = ms
+    ms, value = job_rate(ms, N * args.steps, dist, device="cuda")
     ms_per_step = ms / args.steps
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
 
-    # kernel duration per launch for the roofline (events around each launch)
-    per = time_steps(lat, min(args.steps, 500), 0, per_launch=True)
-    k_ms = statistics.mean(per)
+    # kernel duration for the roofline: the timed region holds only step launches, so its CUDA-event
+    # time / launches is the average launch duration (any gap between launches included)
+    k_ms = local_ms / args.steps
     achieved = bytes_per_lup * N / (k_ms * 1e-3) / 1e9
+    # the same kernel with an event pair around each launch (no overlap between launches), for reference
+    k_iso = statistics.mean(time_steps(lat, min(args.steps, 500), 0, per_launch=True))
 
     kernel = "k_step<%s,%s,%s,%s,force>" % (lname, args.precision, args.closure.upper(), args.formula.upper())
     out = {
@@ -367,7 +381,7 @@ def run_ours(args):
                      "traffic": captured_traffic(kernel),
                      "peak_kind": peak_kind, "kernel": kernel,
                      "bytes_per_lup": bytes_per_lup,
-                     "kernel_ms": round(k_ms, 5)},
+                     "kernel_ms": round(k_ms, 5), "kernel_ms_isolated_launch": round(k_iso, 5)},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
@@ -380,7 +394,7 @@ def run_ours(args):
                       "d2h_bytes_per_step": d2h}
         out["alu_peaks"] = alu_peaks()
         if not args.no_variants:
-            out["variants"] = variants(args, hbm)
+            out["variants"] = variants(args, hbm, out["alu_peaks"])
         if world == 1:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)
@@ -390,7 +404,18 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def variants(args, hbm):
+def fp64_alu_counts():
+    """FP64 flops and FP64-pipe instructions per node update of the FP64 Yu-route step kernel,
+    from the committed ncu capture (profiles/fp64_alu.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_alu.json")) as fh:
+            doc = json.load(fh)
+        return float(doc["fp64_flops_per_lup"]), float(doc["fp64_instructions_per_lup"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def variants(args, hbm, peaks=None):
     """The other (formula x form) pairs and the other workloads, each with its own timing."""
     import torch
 
@@ -403,6 +428,15 @@ def variants(args, hbm):
         n = steps if precision != "fp64" else max(5, steps // 10)
         k_ms = statistics.mean(time_steps(lat, n, max(3, args.warmup // 10), per_launch=True))
         res["channel"]["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
+        counts = fp64_alu_counts()
+        if precision == "fp64" and formula == "yu" and counts and peaks and peaks.get("fp64_fma_tflops"):
+            # the FP64 path is bound by the FP64 pipe: its arithmetic roofline
+            mlups = res["channel"]["fp64_yu"]["MLUPS"]
+            pk = peaks["fp64_fma_tflops"]
+            res["channel"]["fp64_yu"]["alu"] = {
+                "bound": "alu", "fp64_flops_per_lup": counts[0], "achieved_tflops": round(mlups * counts[0] / 1e6, 4),
+                "peak_tflops": pk, "frac": round(mlups * counts[0] / 1e6 / pk, 4),
+                "fp64_pipe_frac": round(mlups * 1e6 * counts[1] / (pk * 1e12 / 2), 4)}
         lat.close()
         torch.cuda.empty_cache()
     # Smagorinsky variants on the same channel: the lagged closure (tau stored from the previous

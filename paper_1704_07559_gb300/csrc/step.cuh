@@ -226,6 +226,31 @@ __device__ __forceinline__ void back_transform(const R (&D)[L::Q], R (&out)[L::Q
     });
 }
 
+// Even and odd parts of out_i = sum_k T_ki D_k over the moments whose bit is set in USE: the rest
+// population gets E0, and each opposite pair p = (a, b) gets out_a = E_p + O_p, out_b = E_p - O_p.
+template <class L, uint32_t USE, class R>
+__device__ __forceinline__ void back_transform_eo(const R (&D)[L::Q], R& E0, R (&E)[L::NP], R (&O)[L::NP]) {
+    R r = nzero<R>();
+    sfor<L::Q>([&](auto k) {
+        if constexpr ((USE >> CV(k)) & 1u) r = cadd<L::T(CV(k), 0)>(r, D[k]);
+    });
+    E0 = r;
+    sfor<L::NP>([&](auto p) {
+        constexpr int a = L::pa(CV(p));
+        R e = nzero<R>(), o = nzero<R>();
+        sfor<L::Q>([&](auto k) {
+            if constexpr ((USE >> CV(k)) & 1u) {
+                if constexpr (even_moment<L>(CV(k)))
+                    e = cadd<L::T(CV(k), a)>(e, D[k]);
+                else
+                    o = cadd<L::T(CV(k), a)>(o, D[k]);
+            }
+        });
+        E[p] = e;
+        O[p] = o;
+    });
+}
+
 template <class L>
 __host__ __device__ constexpr uint32_t mask_nonconserved() {
     uint32_t m = 0;
@@ -463,6 +488,27 @@ __device__ __forceinline__ void contract(const R (&v)[L::Q], R (&N)[L::NS]) {
         sfor<L::Q>([&](auto i) { acc = cadd<L::c(CV(i), a) * L::c(CV(i), b)>(acc, v[i]); });
         N[cpt] = acc;
     });
+}
+
+// N_c = sum_i c_ia c_ib v_i for a field given by its opposite-pair even parts E_p: c_ia c_ib is
+// even under c -> -c, so the odd parts cancel and each pair counts twice (the rest has c = 0).
+template <class L, class R>
+__device__ __forceinline__ void contract_even(const R (&E)[L::NP], R (&N)[L::NS]) {
+    sfor<L::NS>([&](auto cpt) {
+        constexpr int a = strain_axis<L>(CV(cpt), 0), b = strain_axis<L>(CV(cpt), 1);
+        R acc = nzero<R>();
+        sfor<L::NP>([&](auto p) {
+            acc = cadd<L::c(L::pa(CV(p)), a) * L::c(L::pa(CV(p)), b)>(acc, E[p]);
+        });
+        N[cpt] = R(2.0f) * acc;
+    });
+}
+
+template <class L>
+__host__ __device__ constexpr bool viscous_moments_even() {
+    for (int k = 0; k < L::Q; ++k)
+        if (L::viscous(k) && !even_moment<L>(k)) return false;
+    return true;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -850,7 +896,9 @@ __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS],
 
 // Pre-collision populations of node (x,y,z).  Interior rows (y, z away from the faces, and x
 // away from non-periodic x faces) read population i at node + (x wrap) - c_iy nx - c_iz nx ny,
-// the last two terms being the same for the whole warp; other nodes take the general rule:
+// the last two terms being the same for the whole warp; nodes on a periodic boundary row or plane
+// with no wall next to them read the same way with the y and z wraps applied by index (a separate
+// branch, so the interior code stays as short); the rest take the general rule:
 // periodic faces wrap, a population whose source lies behind a wall is reflected from the
 // opposite population of the same node, plus the moving-wall term when it crosses exactly one
 // moving face.
@@ -861,6 +909,32 @@ __device__ __forceinline__ bool interior_rows(const StepArgs<RS>& a, int xlo, in
     if constexpr (L::D == 3) fast = fast && z > 0 && z < a.nz - 1;
     return fast;
 }
+
+// no wall face next to the node (its periodic faces wrap by index)
+template <class L, class ST, class RS>
+__device__ __forceinline__ bool no_wall_next(const StepArgs<RS>& a, int x, int y, int z) {
+    const int w = a.wall_mask;  // bit f: face f (-x, +x, -y, +y, -z, +z) is a wall
+    bool ok = !(w & 3) || (x > 0 && x < a.nx - 1);
+    ok = ok && (!(w & 12) || (y > 0 && y < a.ny - 1));
+    if constexpr (L::D == 3) ok = ok && (!(w & 48) || (z > 0 && z < a.nz - 1));
+    return ok;
+}
+
+// neighbour offsets along y and z with the periodic wrap: the source of c = +1 is one step back
+struct WrapYZ {
+    int ym, yp, zm, zp;
+    __device__ __forceinline__ WrapYZ(int y, int z, int nx, int ny, int nz) {
+        const int nxy = nx * ny;
+        ym = y == 0 ? (ny - 1) * nx : -nx;
+        yp = y == ny - 1 ? -(ny - 1) * nx : nx;
+        zm = z == 0 ? (nz - 1) * nxy : -nxy;
+        zp = z == nz - 1 ? -(nz - 1) * nxy : nxy;
+    }
+    template <int cy, int cz>
+    __device__ __forceinline__ int off() const {
+        return (cy > 0 ? ym : (cy < 0 ? yp : 0)) + (cz > 0 ? zm : (cz < 0 ? zp : 0));
+    }
+};
 
 template <class L, class ST, class RS>
 __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
@@ -904,12 +978,21 @@ template <class L, class ST, class RS>
 __device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
     const int nx = a.nx, nxy = a.nx * a.ny;
     const int node = z * nxy + y * nx + x;
+    const int dxm = x == 0 ? nx - 1 : -1;      // source of c_x = +1: x - 1 (wrapped)
+    const int dxp = x == nx - 1 ? 1 - nx : 1;  // source of c_x = -1: x + 1 (wrapped)
     if (interior_rows<L, ST>(a, x, x, y, z)) {
-        const int dxm = x == 0 ? nx - 1 : -1;      // source of c_x = +1: x - 1 (wrapped)
-        const int dxp = x == nx - 1 ? 1 - nx : 1;  // source of c_x = -1: x + 1 (wrapped)
         sfor<L::Q>([&](auto i) {
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
             const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) - (cy * nx + cz * nxy);
+            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
+        });
+        return;
+    }
+    if (no_wall_next<L, ST>(a, x, y, z)) {  // on a periodic boundary row or plane: wrap y and z too
+        const WrapYZ w(y, z, nx, a.ny, a.nz);
+        sfor<L::Q>([&](auto i) {
+            constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+            const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) + w.template off<cy, cz>();
             f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
         });
         return;
@@ -1108,22 +1191,43 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
                 else
                     Dv[k] = R(0.0f);
             });
-            R Ov[Q];
-            Xf<L>::template backward<mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Om);
-            Xf<L>::template backward<mask_viscous<L>()>(Dv, Ov);
+            // Omega = Omega_f + s_nu Omega_v in opposite-pair even / odd parts; the viscous moments
+            // are all even, so Omega_v has no odd part, and S needs only the even parts
+            static_assert(viscous_moments_even<L>(), "viscous moments must be even");
+            R Ef0, Ef[NP], Of[NP], Ev0, Ev[NP], Ovd[NP];
+            back_transform_eo<L, mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Ef0, Ef, Of);
+            back_transform_eo<L, mask_viscous<L>()>(Dv, Ev0, Ev, Ovd);
             R Nf[NS], Nv[NS], A[NS], B[NS];
-            contract<L>(Om, Nf);
-            contract<L>(Ov, Nv);
+            contract_even<L>(Ef, Nf);
+            contract_even<L>(Ev, Nv);
 #pragma unroll
             for (int c = 0; c < NS; ++c) {
                 A[c] = kS * Nf[c];
                 B[c] = kS * Nv[c];
             }
+            // f* = f - Omega_f + Fbar - s_nu Omega_v: everything but the last term is folded into f
+            // now, so only f and Omega_v stay live across the closure
+            f[0] -= Ef0;
+            if constexpr (FORCE) f[0] += F0;
+            sfor<NP>([&](auto p) {
+                R da = Ef[p] + Of[p], db = Ef[p] - Of[p];
+                if constexpr (FORCE) {
+                    da = fma(R(-0.5f), PF[p] + DF[p], da);
+                    db = fma(R(-0.5f), PF[p] - DF[p], db);
+                }
+                f[L::pa(CV(p))] -= da;
+                f[L::pb(CV(p))] -= db;
+            });
             tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu, node, tau_prev);
             if (a.readout) goto readout;
-            sfor<Q>([&](auto i) { out[i] = fma(snu, Ov[i], Om[i]); });
+            out[0] = snu * Ev0;
+            sfor<NP>([&](auto p) {
+                const R e = snu * Ev[p];
+                out[L::pa(CV(p))] = e;
+                out[L::pb(CV(p))] = e;
+            });
         }
-        if constexpr (FORCE) {  // f* = f - Omega + Fbar
+        if constexpr (FORCE && CLOSURE == CL_NEWTON) {  // f* = f - Omega + Fbar
             out[0] -= F0;
             sfor<NP>([&](auto p) {
                 out[L::pa(CV(p))] = fma(R(-0.5f), PF[p] + DF[p], out[L::pa(CV(p))]);
