@@ -1296,6 +1296,26 @@ __global__ void __launch_bounds__(128, LBM_VW2_MIN_BLOCKS) k_step_pair(const Ste
     step_nodes<L, ST, CLOSURE, FORMULA, FORCE, 2>(a);
 }
 
+// Two x-adjacent nodes per thread that share the pull (paired loads where c_x = 0, adjacent
+// scalar loads otherwise) and then collide one after the other in scalar arithmetic.
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__global__ void __launch_bounds__(128) k_step_pair_seq(const StepArgs<typename Store<ST>::R> a) {
+    pdl_wait();
+    pdl_release();
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    F2 f2[L::Q];
+    pull2<L, ST>(a, x, y, z, f2);
+    const int node = (z * a.ny + y) * a.nx + x;
+    float f[L::Q];
+    sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
+    step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, node);
+    sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
+    step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, node + 1);
+}
+
 // ------------------------------------------------------------------------------------------
 // initialisation from (drho, u, grad u), computed in double, un-streamed into the buffer
 

@@ -153,6 +153,12 @@ CASES = [
     (19, (150, 7, 5), "bf16s", "smag", "chai", dict(tau=0.51)),
     (19, (64, 6, 6), "fp16s", "newton", "chai", dict(bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
                                                       force=[1e-5, 0, 0])),
+    # odd nx: 16-bit storage on the one-node kernel (even nx takes two nodes per thread)
+    (19, (33, 17, 5), "bf16s", "smag", "yu", dict(tau=0.51, force_field=True)),
+    (19, (33, 8, 6), "fp16s", "smag", "chai", dict(tau=0.51, bc=["wall"] * 2 + ["periodic"] * 4)),
+    # even nx with walls at x: the two-node kernel's general pull at the x faces
+    (19, (40, 8, 6), "fp16s", "smag", "yu", dict(tau=0.51, bc=["wall"] * 2 + ["periodic"] * 2 + ["wall", "lid"],
+                                                  lid={5: (0.04, 0.0, 0.0)})),
     (9, (150, 37, 1), "fp64", "powerlaw", "chai", dict(bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)},
                                                        pl=(0.5, 7e-4), tau=1.0)),
     (9, (150, 37, 1), "fp32", "powerlaw", "chai", dict(bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)},
