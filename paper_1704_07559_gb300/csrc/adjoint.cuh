@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) k_adjoint_step(const AdjArgs<typename Sto
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.st.nx || y >= a.st.ny) return;
-    const int N = a.st.nx * a.st.ny * a.st.nz;
+    const long long N = (long long)a.st.nx * a.st.ny * a.st.nz;  // component offsets d*N exceed 2^31
     const int node = (z * a.st.ny + y) * a.st.nx + x;
     R p[19], F[3], lam[19];
     pull<D3Q19, ST>(a.st, x, y, z, p);
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(128) k_functional(const AdjArgs<typename Store
     const bool active = x < a.st.nx && y < a.st.ny;
     double ell = 0.0;
     if (active) {
-        const int N = a.st.nx * a.st.ny * a.st.nz;
+        const long long N = (long long)a.st.nx * a.st.ny * a.st.nz;  // component offsets d*N exceed 2^31
         const int node = (z * a.st.ny + y) * a.st.nx + x;
         R p[19], F[3];
         pull<D3Q19, ST>(a.st, x, y, z, p);

@@ -1050,7 +1050,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     using RS = typename Store<ST>::R;
     using R = std::conditional_t<VW == 2, F2, RS>;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
-    const int N = a.nx * a.ny * a.nz;
+    const long long N = (long long)a.nx * a.ny * a.nz;  // component offsets c*N exceed 2^31 on big grids
 
     R P[NP], Dd[NP];
     sfor<NP>([&](auto p) {
@@ -1330,7 +1330,8 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
-    const int nx = a.nx, ny = a.ny, nz = a.nz, N = nx * ny * nz;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long N = (long long)nx * ny * nz;  // component offsets (up to 8N) exceed 2^31 on big grids
     const int node = (z * ny + y) * nx + x;
     const double r0 = a.rho0, ir0 = a.inv_rho0;
     double j[3] = {0, 0, 0}, F[3] = {0, 0, 0};
@@ -1462,7 +1463,7 @@ template <class L, class ST>
 __global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename Store<ST>::R> a, double* __restrict__ partial) {
     using R = typename Store<ST>::R;
     constexpr int D = L::D;
-    const int N = a.nx * a.ny * a.nz;
+    const long long N = (long long)a.nx * a.ny * a.nz;  // component offsets c*N exceed 2^31 on big grids
     const int rows = a.ny * a.nz;
     Comp<R> acc[1 + D];
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
