@@ -466,10 +466,11 @@ def variants(args, hbm, peaks=None):
         del u_ref, S_ref
         torch.cuda.empty_cache()
     # the same channel on D3Q15 (d'Humieres basis; Yu-type formula of the Sec. 5.4 procedure)
-    for formula in ("yu", "chai"):
-        lat = make_lattice("fp32", formula, lattice=15)
+    for precision, formula in (("fp32", "yu"), ("fp32", "chai"), ("fp16s", "yu"), ("fp16s", "chai")):
+        lat = make_lattice(precision, formula, lattice=15)
         k_ms = statistics.mean(time_steps(lat, steps, max(3, args.warmup // 10), per_launch=True))
-        res["channel"]["d3q15_fp32_%s" % formula] = rate(lat.N, k_ms, 2 * 15 * 4, hbm)
+        res["channel"]["d3q15_%s_%s" % (precision, formula)] = rate(lat.N, k_ms, 2 * 15 * (4 if precision == "fp32" else 2),
+                                                                    hbm)
         lat.close()
         torch.cuda.empty_cache()
     for name, fn in (("box512", box512), ("precision64", precision64), ("cavity4096", cavity4096),
@@ -741,7 +742,7 @@ def main():
     ap.add_argument("--closure", default="smag", choices=["smag", "smag_lagged", "smag_dev"],
                     help="the channel's Smagorinsky closure: implicit (default), lagged or deviatoric closed form")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 15],
-                    help="19: the D3Q19 channel (default); 15: the same channel on D3Q15 (fp32/fp64 only)")
+                    help="19: the D3Q19 channel (default); 15: the same channel on D3Q15")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()

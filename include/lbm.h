@@ -113,7 +113,7 @@ typedef struct lbm_ctx lbm_ctx;
 void lbm_default_params(lbm_params* p);
 
 /* Create a context for an nx x ny x nz lattice (nz = 1 for D2Q9).
- *  lattice  LBM_D2Q9, LBM_D3Q15 or LBM_D3Q19 (D3Q15: FP64 and FP32 storage only).
+ *  lattice  LBM_D2Q9, LBM_D3Q15 or LBM_D3Q19 (D2Q9: FP64 and FP32 storage only).
  *  rates    q relaxation rates s_0..s_{q-1} of the diagonal collision matrix, eq. (sD3Q15):
  *           the conserved entries (0, 3, 5, 7 in D3Q19 and D3Q15; 0, 3, 5 in D2Q9) must be 0,
  *           every other entry lies in (0, 2).  The viscous entries (9, 11, 13, 14, 15 in D3Q19;
@@ -195,7 +195,7 @@ int lbm_set_state(lbm_ctx* ctx, const void* src);
  * caching pool) or a time-stepping loop with a latency budget (cudaMalloc / cudaFree may
  * synchronise the device and take unbounded time).  No context is used and nothing is allocated:
  * no cudaMalloc, cudaFree or allocating library routine is called.
- *  lattice, nx, ny, nz  as for lbm_create (16-bit storage: D3Q19 only);  p: precision, bc,
+ *  lattice, nx, ny, nz  as for lbm_create (16-bit storage: D3Q19 and D3Q15);  p: precision, bc,
  *           lid_u and rho0 are read;
  *  force    d components of the uniform force density, or NULL;
  *  f        device pointer to one population buffer (q arrays of `stride` elements of the

@@ -139,7 +139,7 @@ bool has_force(const lbm_ctx* c) {
     return c->p.force_field || c->force[0] != 0.0 || c->force[1] != 0.0 || c->force[2] != 0.0;
 }
 
-enum Tag { T_D3Q19_F64, T_D3Q19_F32, T_D3Q19_F16, T_D3Q19_BF16, T_D3Q15_F64, T_D3Q15_F32, T_D2Q9_F64, T_D2Q9_F32, T_NONE };
+enum Tag { T_D3Q19_F64, T_D3Q19_F32, T_D3Q19_F16, T_D3Q19_BF16, T_D3Q15_F64, T_D3Q15_F32, T_D3Q15_F16, T_D3Q15_BF16, T_D2Q9_F64, T_D2Q9_F32, T_NONE };
 
 Tag tag_of(int q, int precision) {
     if (q == 19) {
@@ -153,6 +153,8 @@ Tag tag_of(int q, int precision) {
         switch (precision) {
             case LBM_FP64: return T_D3Q15_F64;
             case LBM_FP32: return T_D3Q15_F32;
+            case LBM_FP16S: return T_D3Q15_F16;
+            case LBM_BF16S: return T_D3Q15_BF16;
         }
     } else if (q == 9) {
         switch (precision) {
@@ -197,6 +199,8 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
         case T_D3Q19_F16: return lbm::step_d3q19_f16(a, c->p.closure, formula, force, c->stream);
         case T_D3Q19_BF16: return lbm::step_d3q19_bf16(a, c->p.closure, formula, force, c->stream);
         case T_D3Q15_F32: return lbm::step_d3q15_f32(a, c->p.closure, formula, force, c->stream);
+        case T_D3Q15_F16: return lbm::step_d3q15_f16(a, c->p.closure, formula, force, c->stream);
+        case T_D3Q15_BF16: return lbm::step_d3q15_bf16(a, c->p.closure, formula, force, c->stream);
         case T_D2Q9_F32: return lbm::step_d2q9_f32(a, c->p.closure, formula, force, c->stream);
         default: return cudaErrorInvalidValue;
     }
@@ -571,6 +575,14 @@ int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad
             e = lbm::init_d3q19_bf16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
                                     static_cast<float*>(tf), c->stream);
             break;
+        case T_D3Q15_F16:
+            e = lbm::init_d3q15_f16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
+            break;
+        case T_D3Q15_BF16:
+            e = lbm::init_d3q15_bf16(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
+                                    static_cast<float*>(tf), c->stream);
+            break;
         case T_D2Q9_F32:
             e = lbm::init_d2q9_f32(a, c->p.closure, drho, u, grad_u, static_cast<const float*>(c->force_field),
                                     static_cast<float*>(tf), c->stream);
@@ -639,6 +651,8 @@ int lbm_sums(lbm_ctx* c, double* out) {
             case T_D3Q19_F16: e = lbm::sums_d3q19_f16(a, c->partial, c->result, c->stream); break;
             case T_D3Q19_BF16: e = lbm::sums_d3q19_bf16(a, c->partial, c->result, c->stream); break;
             case T_D3Q15_F32: e = lbm::sums_d3q15_f32(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_F16: e = lbm::sums_d3q15_f16(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_BF16: e = lbm::sums_d3q15_bf16(a, c->partial, c->result, c->stream); break;
             case T_D2Q9_F32: e = lbm::sums_d2q9_f32(a, c->partial, c->result, c->stream); break;
             default: e = cudaErrorInvalidValue;
         }

@@ -31,6 +31,8 @@ LBM_DECLARE_ENTRY(d3q19_f16, float)
 LBM_DECLARE_ENTRY(d3q19_bf16, float)
 LBM_DECLARE_ENTRY(d3q15_f64, double)
 LBM_DECLARE_ENTRY(d3q15_f32, float)
+LBM_DECLARE_ENTRY(d3q15_f16, float)
+LBM_DECLARE_ENTRY(d3q15_bf16, float)
 LBM_DECLARE_ENTRY(d2q9_f64, double)
 LBM_DECLARE_ENTRY(d2q9_f32, float)
 

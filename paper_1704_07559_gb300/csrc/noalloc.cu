@@ -111,7 +111,7 @@ extern "C" int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_p
         case LBM_BF16S: elem = 2; break;
         default: return LBM_ERR_ARG;
     }
-    if (lattice != LBM_D3Q19 && elem == 2) return LBM_ERR_ARG;
+    if (lattice == LBM_D2Q9 && elem == 2) return LBM_ERR_ARG;
 
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return LBM_ERR_CUDA;
@@ -130,7 +130,9 @@ extern "C" int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_p
         if (lattice == LBM_D2Q9)
             e = run<lbm::D2Q9, float>(a, nb, scratch, s);
         else if (lattice == LBM_D3Q15)
-            e = run<lbm::D3Q15, float>(a, nb, scratch, s);
+            e = p->precision == LBM_FP32    ? run<lbm::D3Q15, float>(a, nb, scratch, s)
+                : p->precision == LBM_FP16S ? run<lbm::D3Q15, __half>(a, nb, scratch, s)
+                                            : run<lbm::D3Q15, __nv_bfloat16>(a, nb, scratch, s);
         else if (p->precision == LBM_FP32)
             e = run<lbm::D3Q19, float>(a, nb, scratch, s);
         else if (p->precision == LBM_FP16S)

@@ -123,3 +123,18 @@ def test_adjoint_rejects_unsupported_setups():
                        bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2)
     with pytest.raises(lbm.LBMError):
         lat2.adjoint(4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_at_rest_is_exactly_zero(precision):
+    """|S| is not differentiable at S = 0 (its derivative is taken as 0 there).  A fluid at rest
+    under a zero force field has S = 0 at every node and step, L = 0, and L is quadratic in g
+    there, so dL/dg = 0: the adjoint must return exact zeros, not NaN."""
+    n = 8
+    g = torch.zeros(3, n, n, n, dtype=torch.float64)
+    lat = lbm.Lattice(19, n, n, n, rates=RATES, precision=precision, closure="smag", smag_cs=CS,
+                      force_field=g)
+    lat.init(np.zeros((n, n, n)), np.zeros((3, n, n, n)))
+    L, grad = lat.adjoint(6, 2)
+    assert L == 0.0
+    assert torch.isfinite(grad).all() and float(grad.abs().max()) == 0.0

@@ -174,6 +174,9 @@ CASES = [
                                                     force=[1e-5, 0, 0], tau=0.51)),
     (15, (33, 17, 5), "fp32", "powerlaw", "chai", dict(force_field=True, pl=(0.7, 0.01), tau=0.7)),
     (15, (11, 10, 9), "fp32", "newton", "yu", dict(bc=["wall"] * 4 + ["periodic"] * 2)),
+    (15, (64, 9, 6), "fp16s", "smag", "yu", dict(tau=0.51, bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+                                                  force=[1e-5, 0, 0])),
+    (15, (33, 9, 6), "bf16s", "smag", "chai", dict(tau=0.51, force_field=True)),
     (19, (130, 9, 6), "fp64", "smag_lagged", "yu", dict(bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
                                                          force=[1e-5, 0, 0], tau=0.51)),
     (19, (130, 9, 6), "fp32", "smag_lagged", "chai", dict(force_field=True, tau=0.51)),

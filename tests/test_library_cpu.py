@@ -75,7 +75,7 @@ def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
     dict(mutate=lambda p: (setattr(p, "precision", 2), setattr(p, "closure", 2))),
     dict(lattice=9, mutate=lambda p: setattr(p, "precision", 2)),
     dict(mutate=lambda p: (setattr(p, "closure", 2), setattr(p, "pl_tau_min", 0.5))),
-    dict(lattice=15, mutate=lambda p: setattr(p, "precision", 2)),       # D3Q15: no 16-bit storage
+    dict(lattice=15, mutate=lambda p: (setattr(p, "precision", 3), setattr(p, "closure", 2))),  # 16-bit power law
     dict(lattice=15, rates=D15[:7] + [0.3] + D15[8:]),                  # D3Q15 conserved j_z rate
     dict(lattice=15, rates=D15[:12] + [1.5] + D15[13:]),                # D3Q15 split viscous rates, Yu
     dict(lattice=15, dims=(8, 8, 0)),

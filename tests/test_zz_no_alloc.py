@@ -59,12 +59,13 @@ CASES = [
          tol=1e-6),
     dict(q=15, dims=(50, 12, 7), precision="fp32", bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
          force=[1e-5, 0.0, 2e-6], tol=1e-6),
+    dict(q=15, dims=(40, 10, 6), precision="bf16s", bc=None, force=[2e-6, 0.0, 0.0], tol=1e-6),
 ]
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", CASES, ids=["d3q19-fp32-channel", "d3q19-fp64-periodic", "d2q9-fp32-lid",
-                                           "d3q15-fp32-channel"])
+                                           "d3q15-fp32-channel", "d3q15-bf16-periodic"])
 def test_matches_lbm_sums_on_two_calls_in_a_row(case):
     """Two calls in a row (before and after a step, so the scratch holds the first call's
     contents when the second runs) agree with lbm_sums within the sums tolerance of the parity
