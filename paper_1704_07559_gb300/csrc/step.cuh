@@ -1438,8 +1438,9 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
 
 // ------------------------------------------------------------------------------------------
 // global sums: each block walks whole rows (fixed assignment, so the result is reproducible);
-// FP32 states accumulate with an error-free two-sum (hi, lo) pair per component, FP64 states in
-// plain FP64; per-block partials go to scratch as FP64 and one ordered pass adds them.
+// each node's totals are formed in the compute type, then FP32 states accumulate them across nodes
+// with an error-free two-sum (hi, lo) pair per component, FP64 states in plain FP64; per-block
+// partials go to scratch as FP64 and one ordered pass adds them.
 
 constexpr int SUM_THREADS = 256;
 
@@ -1471,17 +1472,18 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename St
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             R f[L::Q];
             pull<L, ST, R>(a, x, y, z, f);
+            // the node's own totals in plain arithmetic (19 values of one node), then one
+            // compensated add per component across nodes
+            R m0 = nzero<R>(), mj[3] = {nzero<R>(), nzero<R>(), nzero<R>()};
             sfor<L::Q>([&](auto i) {
-                acc[0].add(f[i]);
-                sfor<D>([&](auto d) {
-                    constexpr int cd = L::c(CV(i), CV(d));
-                    if constexpr (cd == 1) acc[1 + CV(d)].add(f[i]);
-                    if constexpr (cd == -1) acc[1 + CV(d)].add(-f[i]);
-                });
+                m0 += f[i];
+                sfor<D>([&](auto d) { mj[d] = cadd<L::c(CV(i), CV(d))>(mj[d], f[i]); });
             });
             const int n = r * a.nx + x;
+            acc[0].add(m0);
 #pragma unroll
-            for (int d = 0; d < D; ++d) acc[1 + d].add(R(0.5) * (a.force_field ? a.force_field[d * N + n] : a.F[d]));
+            for (int d = 0; d < D; ++d)
+                acc[1 + d].add(fma(R(0.5), a.force_field ? a.force_field[d * N + n] : a.F[d], mj[d]));
         }
     }
     __shared__ double red[SUM_THREADS / 32][1 + D];
