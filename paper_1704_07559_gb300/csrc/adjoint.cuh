@@ -184,21 +184,43 @@ struct AdjArgs {
     StepArgs<R> st;      // lattice, rates, closure, force field; srcp = the state f^n
     const R* lam_in;     // lambda_{n+1}, q arrays of `stride` (step) or unused (functional)
     R* lam_out;          // lambda_n
+    const R* lamp_in[19];  // lam_in + i * stride (filled on the host, see set_lambda)
+    R* lamp_out[19];       // lam_out + i * stride
     R* dF;               // 3 x N accumulator of dL/dF over the current segment
     double* partial;     // functional: one FP64 partial sum per block
 };
 
-// write mu_i to the pull's source node x - c_i (periodic): the transpose of the pull
+// host side: the lambda buffers and their per-population base pointers
+template <class R>
+inline void set_lambda(AdjArgs<R>* a, const R* in, R* out) {
+    a->lam_in = in;
+    a->lam_out = out;
+    for (int i = 0; i < 19; ++i) {
+        a->lamp_in[i] = in ? in + i * a->st.stride : nullptr;
+        a->lamp_out[i] = out ? out + i * a->st.stride : nullptr;
+    }
+}
+
+// write mu_i to the pull's source node x - c_i (periodic): the transpose of the pull.  Nodes away
+// from every face write at node - c_i (a warp-uniform offset); the others wrap by index.
 template <class R>
 __device__ __forceinline__ void push(const AdjArgs<R>& a, int x, int y, int z, const R (&mu)[19]) {
-    const int nx = a.st.nx, ny = a.st.ny, nz = a.st.nz;
+    const int nx = a.st.nx, ny = a.st.ny, nz = a.st.nz, nxy = nx * ny;
+    const int node = (z * ny + y) * nx + x;
+    if (x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && z > 0 && z < nz - 1) {
+        sfor<19>([&](auto i) {
+            constexpr int cx = D3Q19::c(CV(i), 0), cy = D3Q19::c(CV(i), 1), cz = D3Q19::c(CV(i), 2);
+            a.lamp_out[CV(i)][node - (cx + cy * nx + cz * nxy)] = mu[i];
+        });
+        return;
+    }
     sfor<19>([&](auto i) {
         constexpr int cx = D3Q19::c(CV(i), 0), cy = D3Q19::c(CV(i), 1), cz = D3Q19::c(CV(i), 2);
         int tx = x - cx, ty = y - cy, tz = z - cz;
         tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
         ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
         tz = tz < 0 ? tz + nz : (tz >= nz ? tz - nz : tz);
-        a.lam_out[CV(i) * a.st.stride + (tz * ny + ty) * nx + tx] = mu[i];
+        a.lamp_out[CV(i)][(tz * ny + ty) * nx + tx] = mu[i];
     });
 }
 
@@ -220,7 +242,7 @@ __global__ void __launch_bounds__(128) k_adjoint_step(const AdjArgs<typename Sto
     R p[19], F[3], lam[19];
     pull<D3Q19, ST>(a.st, x, y, z, p);
     for (int d = 0; d < 3; ++d) F[d] = a.st.force_field[d * N + node];
-    sfor<19>([&](auto i) { lam[i] = a.lam_in[CV(i) * a.st.stride + node]; });
+    sfor<19>([&](auto i) { lam[i] = a.lamp_in[CV(i)][node]; });
     NodeFwd<R> st;
     node_forward<CLOSURE>(p, F, a.st, st);
     R mu[19], Fb[3];

@@ -310,8 +310,7 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
     a.partial = partial;
     // the functional at f^T: loss partials, lambda_T, dF
     set_buffers(c, &a.st, fcur, nullptr);
-    a.lam_in = nullptr;
-    a.lam_out = lam[0];
+    lbm::set_lambda(&a, static_cast<const R*>(nullptr), lam[0]);
     int nb = 0;
     if constexpr (F64)
         e = lbm::adj_functional_f64(a, c->p.closure, s, &nb);
@@ -337,8 +336,7 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
         }
         for (int n = k1 - 1; n >= k0; --n) {
             set_buffers(c, &a.st, states[n - k0], nullptr);
-            a.lam_in = lam[lc];
-            a.lam_out = lam[1 - lc];
+            lbm::set_lambda(&a, static_cast<const R*>(lam[lc]), lam[1 - lc]);
             if constexpr (F64)
                 e = lbm::adj_step_f64(a, c->p.closure, s);
             else
