@@ -233,6 +233,8 @@ struct AdjTypes {
 template <class ST, int CLOSURE>
 __global__ void __launch_bounds__(128) k_adjoint_step(const AdjArgs<typename Store<ST>::R> a) {
     using R = typename Store<ST>::R;
+    pdl_wait();     // lambda_{n+1} and the recomputed state are complete and visible from here on
+    pdl_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;

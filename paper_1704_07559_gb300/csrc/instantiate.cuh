@@ -55,24 +55,6 @@ cudaError_t launch_async(const StepArgs<typename Store<ST>::R>& a, cudaStream_t 
     return cudaGetLastError();
 }
 
-// Programmatic dependent launch of a step kernel: consecutive steps overlap launch and block
-// scheduling with the previous step's tail (the kernel waits for the previous one before its
-// first load).
-template <class K, class A>
-cudaError_t launch_pdl(K kernel, dim3 g, dim3 b, cudaStream_t s, const A& a) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = g;
-    cfg.blockDim = b;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, a);
-}
-
 template <class L, class ST, int C, int F, bool FO>
 cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
     // 16-bit storage (issue-bound): two nodes per thread sharing the pull when nx is even

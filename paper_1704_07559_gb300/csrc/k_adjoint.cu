@@ -22,11 +22,8 @@ template <class ST>
 static cudaError_t step_impl(const AdjArgs<typename Store<ST>::R>& a, int closure, cudaStream_t s) {
     dim3 g, b;
     lattice_grid(a.st.nx, a.st.ny, a.st.nz, &g, &b);
-    if (closure == CL_SMAG)
-        k_adjoint_step<ST, CL_SMAG><<<g, b, 0, s>>>(a);
-    else
-        k_adjoint_step<ST, CL_NEWTON><<<g, b, 0, s>>>(a);
-    return cudaGetLastError();
+    if (closure == CL_SMAG) return launch_pdl(k_adjoint_step<ST, CL_SMAG>, g, b, s, a);
+    return launch_pdl(k_adjoint_step<ST, CL_NEWTON>, g, b, s, a);
 }
 
 template <class R>

@@ -17,6 +17,24 @@ inline void lattice_grid(int nx, int ny, int nz, dim3* grid, dim3* block) {
     *grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
 }
 
+// Programmatic dependent launch of a step (or adjoint step) kernel: consecutive steps overlap launch and block
+// scheduling with the previous step's tail (the kernel waits for the previous one before its
+// first load).
+template <class K, class A>
+cudaError_t launch_pdl(K kernel, dim3 g, dim3 b, cudaStream_t s, const A& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in scratch
 
 #define LBM_DECLARE_ENTRY(TAG, R)                                                                         \
