@@ -1297,9 +1297,11 @@ __global__ void __launch_bounds__(128, LBM_VW2_MIN_BLOCKS) k_step_pair(const Ste
 }
 
 // Two x-adjacent nodes per thread that share the pull (paired loads where c_x = 0, adjacent
-// scalar loads otherwise) and then collide one after the other in scalar arithmetic.
+// scalar loads otherwise) and then collide one after the other in scalar arithmetic.  Bound to 7
+// resident blocks per SM (72 registers; a few spilled values): measured faster than the 80
+// registers and 6 blocks it takes unbounded, and than 64 registers with more spills.
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128) k_step_pair_seq(const StepArgs<typename Store<ST>::R> a) {
+__global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typename Store<ST>::R> a) {
     pdl_wait();
     pdl_release();
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
