@@ -154,7 +154,8 @@ def make_lattice(precision="fp32", formula="yu", dims=(NX, NY, NZ), lattice=19, 
 
 
 def time_steps(lat, steps, warmup, per_launch=False):
-    """Device time of `steps` lattice steps (ms) via CUDA events on the library's stream."""
+    """Device time of `steps` lattice steps (ms) via CUDA events on the library's stream; with
+    per_launch, a list of each launch's time (an event pair around every launch)."""
     import torch
 
     s = lat.stream
@@ -426,7 +427,7 @@ def variants(args, hbm, peaks=None):
                                ("bf16s", "chai"), ("fp64", "yu"), ("fp64", "chai")):
         lat = make_lattice(precision, formula)
         n = steps if precision != "fp64" else max(5, steps // 10)
-        k_ms = statistics.mean(time_steps(lat, n, max(3, args.warmup // 10), per_launch=True))
+        k_ms = step_ms(lat, n, max(3, args.warmup // 10))
         res["channel"]["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
         counts = fp64_alu_counts()
         if precision == "fp64" and formula == "yu" and counts and peaks and peaks.get("fp64_fma_tflops"):
@@ -451,7 +452,7 @@ def variants(args, hbm, peaks=None):
         ref.close()
         for closure, extra in (("smag_lagged", 8), ("smag_dev", 0)):
             lat = make_lattice("fp32", formula, closure=closure)
-            k_ms = statistics.mean(time_steps(lat, steps, max(3, args.warmup // 10), per_launch=True))
+            k_ms = step_ms(lat, steps, max(3, args.warmup // 10))
             row = rate(lat.N, k_ms, BYTES_PER_LUP["fp32"] + extra, hbm)
             lat.close()
             lat = make_lattice("fp32", formula, closure=closure)
@@ -468,7 +469,7 @@ def variants(args, hbm, peaks=None):
     # the same channel on D3Q15 (d'Humieres basis; Yu-type formula of the Sec. 5.4 procedure)
     for precision, formula in (("fp32", "yu"), ("fp32", "chai"), ("fp16s", "yu"), ("fp16s", "chai")):
         lat = make_lattice(precision, formula, lattice=15)
-        k_ms = statistics.mean(time_steps(lat, steps, max(3, args.warmup // 10), per_launch=True))
+        k_ms = step_ms(lat, steps, max(3, args.warmup // 10))
         res["channel"]["d3q15_%s_%s" % (precision, formula)] = rate(lat.N, k_ms, 2 * 15 * (4 if precision == "fp32" else 2),
                                                                     hbm)
         lat.close()
@@ -481,6 +482,12 @@ def variants(args, hbm, peaks=None):
             res[name] = {"error": repr(e)[:300]}
         torch.cuda.empty_cache()
     return res
+
+
+def step_ms(lat, steps, warmup):
+    """Average time of one step among `steps` back-to-back step launches (ms): the same measure
+    as the headline's timed region."""
+    return time_steps(lat, steps, warmup) / steps
 
 
 def rate(N, k_ms, bytes_per_lup, hbm):
@@ -514,7 +521,7 @@ def box512(args, hbm):
     for precision in ("fp32", "fp16s", "bf16s"):
         for formula in ("yu", "chai"):
             lat = box_lattice(n, precision, formula, 8, 0.03, 4)
-            k_ms = statistics.mean(time_steps(lat, 30, 5, per_launch=True))
+            k_ms = step_ms(lat, 30, 5)
             out["%s_%s" % (precision, formula)] = rate(lat.N, k_ms, BYTES_PER_LUP[precision], hbm)
             lat.close()
             torch.cuda.empty_cache()
@@ -577,7 +584,7 @@ def cavity4096(args, hbm):
     for nidx in (0.5, 1.0, 1.5):
         for formula in ("chai", "yu"):
             lat = cavity_lattice(4096, nidx, formula)
-            k_ms = statistics.mean(time_steps(lat, 50, 20, per_launch=True))
+            k_ms = step_ms(lat, 50, 20)
             out["n%.1f_%s" % (nidx, formula)] = rate(lat.N, k_ms, 72, hbm)
             lat.close()
     return out
@@ -667,7 +674,7 @@ def tgv32(args, hbm):
     n, tau, T = TGV_N, TGV_TAU, TGV_STEPS
     lat = tgv_lattice()
     S0 = lat.strain_rate("yu").abs().max().item()
-    k_ms = statistics.mean(time_steps(lat, T, 0, per_launch=True))
+    k_ms = step_ms(lat, T, 0)
     Sy, Sc = lat.strain_rate("yu"), lat.strain_rate("chai")
     nu, kk = (tau - 0.5) / 3, 2 * np.pi / n
     ratio = Sy.abs().max().item() / S0 / np.exp(-3 * nu * kk * kk * T)
