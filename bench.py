@@ -57,8 +57,9 @@ def env_int(name, default):
 
 
 def captured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the capture
-    is of another kernel or the kernel sources changed since it was taken."""
+    """DRAM bytes per lattice step of `kernel` from the committed ncu capture (the capture's bytes
+    divided by the steps its launch ran), or None when the capture is of another kernel or the
+    kernel sources changed since it was taken."""
     import hashlib
 
     try:
@@ -69,7 +70,7 @@ def captured_traffic(kernel):
             with open(os.path.join(ROOT, src), "rb") as fh:
                 h.update(fh.read())
         if doc["kernel"] == kernel and h.hexdigest() == doc["sources_sha256"]:
-            return int(doc["dram_bytes_per_launch"])
+            return int(doc["dram_bytes_per_step"])
     except (OSError, ValueError, KeyError):
         pass
     return None
@@ -172,8 +173,7 @@ def time_steps(lat, steps, warmup, per_launch=False):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(s)
-    for _ in range(steps):
-        lat.step(1)
+    lat.step(steps)
     t1.record(s)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1)
@@ -353,21 +353,27 @@ def run_ours(args):
         dist.barrier()
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    steps0, launches0 = lat.stats()
     with ClockSampler(gpu_index) as clk:
         ms = time_steps(lat, args.steps, 0)
         torch.cuda.synchronize()
+    steps1, launches1 = lat.stats()
+    launches = launches1 - launches0
+    assert steps1 - steps0 == args.steps
     local_ms = ms
     ms, value = job_rate(ms, N * args.steps, dist, device="cuda")
     ms_per_step = ms / args.steps
 
-    # kernel duration for the roofline: the timed region holds only step launches, so its CUDA-event
-    # time / launches is the average launch duration (any gap between launches included)
+    # kernel time per step for the roofline: the timed region holds only step launches (one per step,
+    # or multi-step launches), so its CUDA-event time / steps is the time of one step's work
     k_ms = local_ms / args.steps
     achieved = bytes_per_lup * N / (k_ms * 1e-3) / 1e9
-    # the same kernel with an event pair around each launch (no overlap between launches), for reference
+    # one-step launches with an event pair around each (no overlap between launches), for reference
     k_iso = statistics.mean(time_steps(lat, min(args.steps, 500), 0, per_launch=True))
 
-    kernel = "k_step<%s,%s,%s,%s,force>" % (lname, args.precision, args.closure.upper(), args.formula.upper())
+    streamed = launches < args.steps
+    kernel = "%s<%s,%s,%s,%s,force>" % ("k_step_stream" if streamed else "k_step", lname, args.precision,
+                                         args.closure.upper(), args.formula.upper())
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
@@ -382,8 +388,9 @@ def run_ours(args):
                      "traffic": captured_traffic(kernel),
                      "peak_kind": peak_kind, "kernel": kernel,
                      "bytes_per_lup": bytes_per_lup,
-                     "kernel_ms": round(k_ms, 5), "kernel_ms_isolated_launch": round(k_iso, 5)},
-        "gpu_launches": args.steps,
+                     "per": "lattice step (%d steps per launch)" % round(args.steps / max(launches, 1)),
+                     "kernel_ms": round(k_ms, 5), "one_step_launches_ms": round(k_iso, 5)},
+        "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     if rank == 0 and args.quick:

@@ -163,8 +163,48 @@ int lbm_init(lbm_ctx* ctx, const double* drho, const double* u, const double* gr
 
 /* Advance n >= 0 time steps: each step pulls f from the current buffer, collides every node
  * with S and tau formed by p->formula, and writes f* to the other buffer, which becomes current.
- * n = 0 does nothing. */
+ * n = 0 does nothing.  Asynchronous on the bound stream.  The result does not depend on the
+ * schedule (lbm_set_schedule): each node's arithmetic is the same whether the steps are launched
+ * one at a time or several per launch.  A multi-step launch orders its tiles through
+ * library-owned counters with bounded waits; a wait that runs out (none does while the launch
+ * has the GPU to itself) is reported by the next lbm_sums or lbm_status as LBM_ERR_STATE. */
 int lbm_step(lbm_ctx* ctx, int n);
+
+/* How lbm_step(n >= 2) launches its steps.
+ *  LBM_SCHEDULE_AUTO      several steps per launch when the storage is FP32/FP16S/BF16S, the
+ *                         closure is not LBM_SMAG_LAGGED, the lattice has at most 2^23 nodes and
+ *                         more units (a z plane times a band of y rows of about 1024-4096 nodes)
+ *                         than the GPU holds resident blocks; one launch per step otherwise (the
+ *                         default).  On larger lattices a step boundary costs less than the
+ *                         multi-step launch's synchronisation.
+ *  LBM_SCHEDULE_PER_STEP  one launch per step.
+ *  LBM_SCHEDULE_STREAM    several steps per launch wherever the storage and closure allow it,
+ *                         whatever the lattice size.
+ *  LBM_SCHEDULE_STALL_CHECK  diagnostic of the bounded waits, one-shot: the next lbm_step(n >= 2)
+ *                         that can run several steps per launch starts that launch one step
+ *                         ahead, so that every dependency wait runs out (about two seconds);
+ *                         the launch ends, lbm_status then reports LBM_ERR_STATE, the state is
+ *                         invalid and the schedule is back to LBM_SCHEDULE_AUTO.
+ * A launch of several steps cuts the lattice into units (one z plane by a band of y rows, all of
+ * x); a unit runs step k once its neighbouring units (z +-1, band +-1, periodically wrapped) have
+ * completed step k-1, so consecutive steps overlap instead of draining the GPU between them.
+ * Errors: LBM_ERR_ARG for an unknown schedule. */
+#define LBM_SCHEDULE_AUTO 0
+#define LBM_SCHEDULE_PER_STEP 1
+#define LBM_SCHEDULE_STREAM 2
+#define LBM_SCHEDULE_STALL_CHECK 3
+int lbm_set_schedule(lbm_ctx* ctx, int schedule);
+
+/* Counters since lbm_create: *steps = time steps advanced by lbm_step, *step_launches = step
+ * kernels it launched for them (one per step, or one per multi-step launch).  Either pointer may
+ * be NULL.  Host-side; no synchronisation. */
+int lbm_stats(const lbm_ctx* ctx, int64_t* steps, int64_t* step_launches);
+
+/* Synchronise the bound stream and report the library's asynchronous status: LBM_ERR_CUDA for a
+ * failed kernel, LBM_ERR_STATE (once; the record is then cleared) when a multi-step launch
+ * stopped because a wait for neighbouring units ran out, LBM_OK otherwise (also when nothing is
+ * bound). */
+int lbm_status(lbm_ctx* ctx);
 
 /* Strain rate of the state the next step sees, by `formula` (LBM_YU or LBM_CHAI), with the
  * closure solved as in a step.  S_out: ns x N values of the compute type (ns = 6 in 3D, 3 in
@@ -178,7 +218,7 @@ int lbm_macroscopic(lbm_ctx* ctx, void* drho_out, void* u_out);
 /* Global sums of the state the next step sees, accumulated in FP64 on the device:
  * out[0] = sum delta rho, out[1..d] = sum j (j = sum c f + F/2).  out is a HOST pointer to d+1
  * doubles.  Synchronises the bound stream.  Returns LBM_ERR_NONFINITE (with out filled) if a sum
- * is NaN or infinite. */
+ * is NaN or infinite, LBM_ERR_STATE as lbm_status does. */
 int lbm_sums(lbm_ctx* ctx, double* out);
 
 /* Copy the current buffer's populations to dst / from src as a dense q x N array of the storage

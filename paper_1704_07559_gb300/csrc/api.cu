@@ -2,6 +2,7 @@
 // the kernel instantiations.  No call aborts; every failure returns a status and a message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,6 +33,12 @@ struct lbm_ctx {
     // library-owned scratch: per-block partial sums and the final row
     double* partial;
     double* result;
+    // several steps per launch: synchronisation words (error flag, ticket, per-unit step counts)
+    // and the unit geometry; schedule is one of LBM_SCHEDULE_*
+    int* sync;
+    int stream_rows, stream_tiles;
+    int schedule;
+    long long n_steps, n_step_launches;  // steps advanced and step kernels launched by lbm_step
     char err[512];
 };
 
@@ -165,6 +172,53 @@ Tag tag_of(int q, int precision) {
     return T_NONE;
 }
 
+// Several steps in one launch (float storage; the lagged closure keeps per-node state outside
+// the populations and steps one launch at a time).  Returns cudaErrorNotSupported when the
+// streamed form does not apply or (automatic schedule) is not expected to pay: more than 2^23
+// nodes, or too few units to keep every resident block busy without waiting; the caller then
+// launches step by step.
+cudaError_t run_stream(lbm_ctx* c, int nsteps) {
+    if (c->p.precision == LBM_FP64 || c->p.closure == LBM_SMAG_LAGGED || c->schedule == LBM_SCHEDULE_PER_STEP)
+        return cudaErrorNotSupported;
+    // the stall check starts at step 1 of the launch: the neighbours' step 0 never runs
+    const bool stall = c->schedule == LBM_SCHEDULE_STALL_CHECK;
+    lbm::StepArgs<float> a0, a1;
+    fill_args(c, &a0);
+    a0.readout = 0;
+    a0.S_out = a0.tau_out = a0.drho_out = a0.u_out = nullptr;
+    a1 = a0;
+    set_buffers(c, &a0, c->buf[c->cur], c->buf[1 - c->cur]);
+    set_buffers(c, &a1, c->buf[1 - c->cur], c->buf[c->cur]);
+    const lbm::StreamCtl ctl = {c->sync, nsteps, c->stream_rows, c->stream_tiles, stall ? 1 : 0};
+    const int force = has_force(c) ? 1 : 0, forced = (stall || c->schedule == LBM_SCHEDULE_STREAM) ? 1 : 0;
+    const int cl = c->p.closure, fm = c->p.formula;
+    if (stall) c->schedule = LBM_SCHEDULE_AUTO;
+    switch (tag_of(c->q, c->p.precision)) {
+        case T_D3Q19_F32: return lbm::stream_d3q19_f32(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        case T_D3Q19_F16: return lbm::stream_d3q19_f16(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        case T_D3Q19_BF16: return lbm::stream_d3q19_bf16(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        case T_D3Q15_F32: return lbm::stream_d3q15_f32(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        case T_D3Q15_F16: return lbm::stream_d3q15_f16(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        case T_D3Q15_BF16: return lbm::stream_d3q15_bf16(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        case T_D2Q9_F32: return lbm::stream_d2q9_f32(a0, a1, ctl, cl, fm, force, forced, c->stream);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+// After a synchronisation: LBM_ERR_STATE (and the flag cleared) when a multi-step launch
+// recorded that one of its dependency waits ran out.
+int stream_flag(lbm_ctx* c) {
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, c->sync, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the multi-step status");
+    if (flag) {
+        cudaMemset(c->sync, 0, sizeof(int));
+        return fail(c, LBM_ERR_STATE,
+                    "a multi-step launch stopped: a wait for neighbouring units ran out; the state is invalid");
+    }
+    return LBM_OK;
+}
+
 // step or read-out launch through the right instantiation
 cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, void* drho, void* u,
                      const void* src, void* dst) {
@@ -204,6 +258,33 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
         case T_D2Q9_F32: return lbm::step_d2q9_f32(a, c->p.closure, formula, force, c->stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// n steps from the current buffer (which alternates): several per launch where the schedule
+// allows (in chunks that keep the ticket count below 2^31), one launch per step otherwise.
+// *launches counts the step kernels launched.
+cudaError_t advance(lbm_ctx* c, int n, long long* launches) {
+    int it = 0;
+    if (n >= 2) {
+        const long long units = (long long)c->nz * c->stream_tiles;
+        const int chunk = (int)std::min<long long>(n, 0x7fffffffLL / units);
+        while (n - it >= 2 && chunk >= 2) {
+            const int k = std::min(chunk, n - it);
+            cudaError_t e = run_stream(c, k);
+            if (e == cudaErrorNotSupported) break;
+            if (e != cudaSuccess) return e;
+            if (k & 1) c->cur = 1 - c->cur;
+            it += k;
+            ++*launches;
+        }
+    }
+    for (; it < n; ++it) {
+        cudaError_t e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, c->buf[c->cur], c->buf[1 - c->cur]);
+        if (e != cudaSuccess) return e;
+        c->cur = 1 - c->cur;
+        ++*launches;
+    }
+    return cudaSuccess;
 }
 
 int check_bound(lbm_ctx* c) {
@@ -277,31 +358,34 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
             return lbm::adj_fold_f32(acc, dLdg, c->p.rho0, 3LL * c->N, s);
     };
 
-    // forward T steps from the current state, keeping every seg-th state
+    // forward T steps from the current state, keeping every seg-th state: per segment, the first
+    // step reads the checkpoint into a context buffer, the middle steps ping-pong between the two
+    // context buffers (several per launch where the schedule allows), and the last step writes the
+    // next checkpoint (the last segment ends in a context buffer)
     const void* fcur = c->buf[c->cur];
     if (T > 0) {
         e = cudaMemcpyAsync(cp(0), c->buf[c->cur], state_bytes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
-        fcur = cp(0);
-        int other = c->cur;  // ping-pong through the context's two buffers
-        for (int n = 0; n < T; ++n) {
-            void* dst;
-            if ((n + 1) % seg == 0 && n + 1 < T) {
-                dst = cp((n + 1) / seg);
-            } else {
-                other = (fcur == c->buf[other]) ? 1 - other : other;
-                dst = c->buf[other];
+        for (int k0 = 0; k0 < T; k0 += seg) {
+            const int k1 = (k0 + seg < T) ? k0 + seg : T;
+            const bool to_cp = k1 < T;
+            if (to_cp && k1 - k0 == 1) {  // one-step segments: checkpoint to checkpoint
+                e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, cp(k0 / seg), cp(k1 / seg));
+                if (e != cudaSuccess) return e;
+                continue;
             }
-            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, fcur, dst);
+            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, cp(k0 / seg), c->buf[0]);
             if (e != cudaSuccess) return e;
-            fcur = dst;
-        }
-        if (fcur != c->buf[0] && fcur != c->buf[1]) {
-            e = cudaMemcpyAsync(c->buf[c->cur], fcur, state_bytes, cudaMemcpyDeviceToDevice, s);
+            c->cur = 0;
+            long long launches = 0;
+            e = advance(c, k1 - k0 - 1 - (to_cp ? 1 : 0), &launches);
             if (e != cudaSuccess) return e;
-            fcur = c->buf[c->cur];
+            if (to_cp) {
+                e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, c->buf[c->cur], cp(k1 / seg));
+                if (e != cudaSuccess) return e;
+            }
         }
-        c->cur = fcur == c->buf[0] ? 0 : 1;
+        fcur = c->buf[c->cur];
     }
 
     lbm::AdjArgs<R> a;
@@ -479,12 +563,21 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
             if (!is_finite(p.lid_u[f][k])) return bad("lid");
     if (p.force_field != 0 && p.force_field != 1) return bad("force_field");
 
-    // library-owned scratch for the global sums
+    // units of the multi-step launch: one z plane times enough rows for about 1024 nodes
+    c->stream_rows = nx >= 1024 ? 1 : std::min(ny, 1024 / nx);
+    c->stream_tiles = (ny + c->stream_rows - 1) / c->stream_rows;
+    c->schedule = LBM_SCHEDULE_AUTO;
+
+    // library-owned scratch for the global sums and the multi-step launch
     cudaError_t e = cudaMalloc(&c->partial, sizeof(double) * (size_t)lbm::SUM_BLOCKS * (1 + c->d));
     if (e == cudaSuccess) e = cudaMalloc(&c->result, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->sync, sizeof(int) * (2 + (size_t)nz * c->stream_tiles));
+    if (e == cudaSuccess) e = cudaMemset(c->sync, 0, sizeof(int));
     if (e != cudaSuccess) {
         snprintf(create_err, sizeof(create_err), "lbm_create: scratch allocation failed: %s", cudaGetErrorString(e));
         cudaFree(c->partial);
+        cudaFree(c->result);
+        cudaFree(c->sync);
         delete c;
         return e == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA;
     }
@@ -497,8 +590,33 @@ int lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
     cudaFree(c->partial);
     cudaFree(c->result);
+    cudaFree(c->sync);
     delete c;
     return LBM_OK;
+}
+
+int lbm_stats(const lbm_ctx* c, int64_t* steps, int64_t* step_launches) {
+    if (!c) return LBM_ERR_ARG;
+    if (steps) *steps = c->n_steps;
+    if (step_launches) *step_launches = c->n_step_launches;
+    return LBM_OK;
+}
+
+int lbm_set_schedule(lbm_ctx* c, int schedule) {
+    if (!c) return LBM_ERR_ARG;
+    if (schedule != LBM_SCHEDULE_AUTO && schedule != LBM_SCHEDULE_PER_STEP && schedule != LBM_SCHEDULE_STREAM &&
+        schedule != LBM_SCHEDULE_STALL_CHECK)
+        return fail(c, LBM_ERR_ARG, "lbm_set_schedule: unknown schedule %d", schedule);
+    c->schedule = schedule;
+    return LBM_OK;
+}
+
+int lbm_status(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->bound) return LBM_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_status");
+    return stream_flag(c);
 }
 
 int lbm_layout(const lbm_ctx* c, int* q, int64_t* stride, int* elem_bytes) {
@@ -595,11 +713,11 @@ int lbm_step(lbm_ctx* c, int n) {
     int rc = check_bound(c);
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_ERR_ARG, "lbm_step: n < 0");
-    for (int it = 0; it < n; ++it) {
-        cudaError_t e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, c->buf[c->cur], c->buf[1 - c->cur]);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
-        c->cur = 1 - c->cur;
-    }
+    long long launches = 0;
+    cudaError_t e = advance(c, n, &launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
+    c->n_steps += n;
+    c->n_step_launches += launches;
     return LBM_OK;
 }
 
@@ -660,6 +778,8 @@ int lbm_sums(lbm_ctx* c, double* out) {
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums copy");
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums sync");
+    rc = stream_flag(c);
+    if (rc) return rc;
     for (int k = 0; k <= c->d; ++k)
         if (!is_finite(out[k])) return fail(c, LBM_ERR_NONFINITE, "lbm_sums: non-finite sum %d", k);
     return LBM_OK;

@@ -1,0 +1,3 @@
+// Multi-step (streamed) kernel instantiations for lattice D3Q15 with __half population storage.
+#include "step_stream.cuh"
+LBM_DEFINE_STREAM_ENTRY(d3q15_f16, lbm::D3Q15, __half, false)

@@ -35,6 +35,18 @@ cudaError_t launch_pdl(K kernel, dim3 g, dim3 b, cudaStream_t s, const A& a) {
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+// Several steps in one launch (step_stream.cuh): the library-owned synchronisation words and the
+// unit geometry.  sync[0] is a sticky error flag (a dependency wait ran out), sync[1] the ticket
+// counter and sync[2 + z * tiles_y + ty] the number of steps unit (z, ty) has completed (room for
+// nz * tiles_y units at the given rows); the launcher zeroes sync[1 ..] before each launch.
+struct StreamCtl {
+    int* sync;
+    int steps;       // steps in this launch
+    int rows;        // lattice rows (y) per unit (the launcher may take a multiple)
+    int tiles_y;     // units per z plane: ceil(ny / rows)
+    int first_step;  // 0; 1 only for the diagnostic that makes every dependency wait run out
+};
+
 constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in scratch
 
 #define LBM_DECLARE_ENTRY(TAG, R)                                                                         \
@@ -42,6 +54,18 @@ constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in 
     cudaError_t init_##TAG(const StepArgs<double>& a, int closure, const double* drho, const double* u, \
                            const double* gu, const R* ffield, R* tau_field, cudaStream_t s);             \
     cudaError_t sums_##TAG(const StepArgs<R>& a, double* partial, double* out, cudaStream_t s);
+
+#define LBM_DECLARE_STREAM_ENTRY(TAG, R)                                                                      \
+    cudaError_t stream_##TAG(const StepArgs<R>& a0, const StepArgs<R>& a1, const StreamCtl& c, int closure, \
+                             int formula, int force, int force_stream, cudaStream_t s);
+LBM_DECLARE_STREAM_ENTRY(d3q19_f32, float)
+LBM_DECLARE_STREAM_ENTRY(d3q19_f16, float)
+LBM_DECLARE_STREAM_ENTRY(d3q19_bf16, float)
+LBM_DECLARE_STREAM_ENTRY(d3q15_f32, float)
+LBM_DECLARE_STREAM_ENTRY(d3q15_f16, float)
+LBM_DECLARE_STREAM_ENTRY(d3q15_bf16, float)
+LBM_DECLARE_STREAM_ENTRY(d2q9_f32, float)
+#undef LBM_DECLARE_STREAM_ENTRY
 
 LBM_DECLARE_ENTRY(d3q19_f64, double)
 LBM_DECLARE_ENTRY(d3q19_f32, float)

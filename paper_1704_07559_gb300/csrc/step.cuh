@@ -80,7 +80,10 @@ __device__ __forceinline__ constexpr R cst(double c) {
 }
 
 // ------------------------------------------------------------------------------------------
-// storage types: scalar access, and the pair access of the two-node path
+// storage types: scalar access, and the pair access of the two-node path.  ld/ld2 read through
+// the non-coherent path (the buffer is read-only for the whole kernel); ldc/ld2c read through L2
+// only (ld.global.cg), for a kernel that reads populations other blocks of the same kernel wrote
+// after synchronising with them.
 
 template <class ST>
 struct Store;
@@ -88,24 +91,31 @@ template <>
 struct Store<double> {
     using R = double;
     static __device__ __forceinline__ R ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ R ldc(const double* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(double* p, R v) { __stcs(p, v); }
 };
 template <>
 struct Store<float> {
     using R = float;
     static __device__ __forceinline__ R ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ R ldc(const float* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float* p, R v) { __stcs(p, v); }
     // aligned pair p[0], p[1] (p 8-byte aligned)
     static __device__ __forceinline__ F2 ld2(const float* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
+    static __device__ __forceinline__ F2 ld2c(const float* p) { return F2(__ldcg(reinterpret_cast<const float2*>(p))); }
     static __device__ __forceinline__ void st2(float* p, F2 v) { __stcs(reinterpret_cast<float2*>(p), v.v); }
 };
 template <>
 struct Store<__half> {
     using R = float;
     static __device__ __forceinline__ R ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ R ldc(const __half* p) { return __half2float(__ldcg(p)); }
     static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ F2 ld2(const __half* p) {
         return F2(__half22float2(__ldg(reinterpret_cast<const __half2*>(p))));
+    }
+    static __device__ __forceinline__ F2 ld2c(const __half* p) {
+        return F2(__half22float2(__ldcg(reinterpret_cast<const __half2*>(p))));
     }
     static __device__ __forceinline__ void st2(__half* p, F2 v) {
         *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
@@ -115,9 +125,13 @@ template <>
 struct Store<__nv_bfloat16> {
     using R = float;
     static __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ R ldc(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ F2 ld2(const __nv_bfloat16* p) {
         return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p))));
+    }
+    static __device__ __forceinline__ F2 ld2c(const __nv_bfloat16* p) {
+        return F2(__bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p))));
     }
     static __device__ __forceinline__ void st2(__nv_bfloat16* p, F2 v) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
@@ -936,7 +950,23 @@ struct WrapYZ {
     }
 };
 
-template <class L, class ST, class RS>
+// population load: COH selects the coherent (L2) path
+template <bool COH, class ST>
+__device__ __forceinline__ typename Store<ST>::R ldp(const ST* p) {
+    if constexpr (COH)
+        return Store<ST>::ldc(p);
+    else
+        return Store<ST>::ld(p);
+}
+template <bool COH, class ST>
+__device__ __forceinline__ F2 ldp2(const ST* p) {
+    if constexpr (COH)
+        return Store<ST>::ld2c(p);
+    else
+        return Store<ST>::ld2(p);
+}
+
+template <class L, class ST, bool COH = false, class RS>
 __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int node = (z * ny + y) * nx + x;
@@ -961,9 +991,9 @@ __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y
             }
         });
         if (nout == 0) {
-            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + (s[2] * ny + s[1]) * nx + s[0]);
+            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + (s[2] * ny + s[1]) * nx + s[0]);
         } else {
-            RS v = Store<ST>::ld(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + node);
+            RS v = ldp<COH>(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + node);
             if (nout == 1 && ((a.lid_mask >> face) & 1)) {
                 const RS cu = RS(L::c(CV(i), 0)) * a.lid[face][0] + RS(L::c(CV(i), 1)) * a.lid[face][1] +
                               RS(L::c(CV(i), 2)) * a.lid[face][2];
@@ -974,7 +1004,7 @@ __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y
     });
 }
 
-template <class L, class ST, class RS>
+template <class L, class ST, bool COH = false, class RS>
 __device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
     const int nx = a.nx, nxy = a.nx * a.ny;
     const int node = z * nxy + y * nx + x;
@@ -984,7 +1014,7 @@ __device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z,
         sfor<L::Q>([&](auto i) {
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
             const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) - (cy * nx + cz * nxy);
-            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
+            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + off);
         });
         return;
     }
@@ -993,16 +1023,17 @@ __device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z,
         sfor<L::Q>([&](auto i) {
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
             const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) + w.template off<cy, cz>();
-            f[i] = Store<ST>::ld(static_cast<const ST*>(a.srcp[CV(i)]) + off);
+            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + off);
         });
         return;
     }
-    pull_general<L, ST>(a, x, y, z, f);
+    pull_general<L, ST, COH>(a, x, y, z, f);
 }
 
 // Two nodes (x0, x0 + 1), x0 even, nx even: populations with c_x = 0 come as one aligned pair,
-// the others as two scalar loads (x wrap applied per node).
-template <class L, class ST>
+// the others as two scalar loads (x wrap applied per node); periodic boundary rows and planes
+// with no wall next to either node wrap y and z by index, as in the one-node pull.
+template <class L, class ST, bool COH = false>
 __device__ __forceinline__ void pull2(const StepArgs<float>& a, int x0, int y, int z, F2 (&f)[L::Q]) {
     const int nx = a.nx, nxy = a.nx * a.ny;
     const int node = z * nxy + y * nx + x0;
@@ -1013,17 +1044,34 @@ __device__ __forceinline__ void pull2(const StepArgs<float>& a, int x0, int y, i
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
             const ST* p = static_cast<const ST*>(a.srcp[CV(i)]) + (node - (cy * nx + cz * nxy));
             if constexpr (cx == 0)
-                f[i] = Store<ST>::ld2(p);
+                f[i] = ldp2<COH>(p);
             else if constexpr (cx > 0)
-                f[i] = F2(Store<ST>::ld(p + dxm), Store<ST>::ld(p));
+                f[i] = F2(ldp<COH>(p + dxm), ldp<COH>(p));
             else
-                f[i] = F2(Store<ST>::ld(p + 1), Store<ST>::ld(p + dxp));
+                f[i] = F2(ldp<COH>(p + 1), ldp<COH>(p + dxp));
+        });
+        return;
+    }
+    if (no_wall_next<L, ST>(a, x0, y, z) && no_wall_next<L, ST>(a, x0 + 1, y, z)) {
+        // on a periodic boundary row or plane: the same loads with the y and z wraps by index
+        const WrapYZ w(y, z, nx, a.ny, a.nz);
+        const int dxm = x0 == 0 ? nx - 1 : -1;
+        const int dxp = x0 + 2 == nx ? 2 - nx : 2;
+        sfor<L::Q>([&](auto i) {
+            constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
+            const ST* p = static_cast<const ST*>(a.srcp[CV(i)]) + (node + w.template off<cy, cz>());
+            if constexpr (cx == 0)
+                f[i] = ldp2<COH>(p);
+            else if constexpr (cx > 0)
+                f[i] = F2(ldp<COH>(p + dxm), ldp<COH>(p));
+            else
+                f[i] = F2(ldp<COH>(p + 1), ldp<COH>(p + dxp));
         });
         return;
     }
     float f0[L::Q], f1[L::Q];
-    pull_general<L, ST>(a, x0, y, z, f0);
-    pull_general<L, ST>(a, x0 + 1, y, z, f1);
+    pull_general<L, ST, COH>(a, x0, y, z, f0);
+    pull_general<L, ST, COH>(a, x0 + 1, y, z, f1);
     sfor<L::Q>([&](auto i) { f[i] = F2(f0[i], f1[i]); });
 }
 
@@ -1473,7 +1521,7 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename St
         const int y = r % a.ny, z = r / a.ny;
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             R f[L::Q];
-            pull<L, ST, R>(a, x, y, z, f);
+            pull<L, ST>(a, x, y, z, f);
             // the node's own totals in plain arithmetic (19 values of one node), then one
             // compensated add per component across nodes
             R m0 = nzero<R>(), mj[3] = {nzero<R>(), nzero<R>(), nzero<R>()};

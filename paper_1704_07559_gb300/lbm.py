@@ -22,11 +22,13 @@ PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2, "bf16s": 3}
 CLOSURE = {"newton": 0, "smag": 1, "powerlaw": 2, "smag_lagged": 3, "smag_dev": 4}
 FORMULA = {"yu": 0, "chai": 1}
 BC = {"periodic": 0, "wall": 1, "lid": 2}
+SCHEDULE = {"auto": 0, "per_step": 1, "stream": 2, "stall_check": 3}
 STORAGE_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_STATE"}
 API = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_layout", "lbm_bind", "lbm_bind_tau", "lbm_init",
        "lbm_step", "lbm_strain_rate", "lbm_macroscopic", "lbm_sums", "lbm_get_state", "lbm_set_state", "lbm_last_error",
-       "lbm_sums_noalloc", "lbm_adjoint_workspace", "lbm_adjoint"]
+       "lbm_sums_noalloc", "lbm_adjoint_workspace", "lbm_adjoint", "lbm_set_schedule", "lbm_status",
+       "lbm_stats"]
 
 
 class LBMError(RuntimeError):
@@ -79,6 +81,9 @@ def lib():
     L.lbm_bind_tau.argtypes = [vp, vp]
     L.lbm_init.argtypes = [vp, vp, vp, vp]
     L.lbm_step.argtypes = [vp, ctypes.c_int]
+    L.lbm_set_schedule.argtypes = [vp, ctypes.c_int]
+    L.lbm_status.argtypes = [vp]
+    L.lbm_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_int, vp, vp]
     L.lbm_macroscopic.argtypes = [vp, vp, vp]
     L.lbm_sums.argtypes = [vp, dp]
@@ -211,6 +216,22 @@ class Lattice:
 
     def step(self, n=1):
         self._check(lib().lbm_step(self.ctx, int(n)))
+        return self
+
+    def set_schedule(self, schedule):
+        """How step(n >= 2) launches: "auto", "per_step" or "stream" (several steps per launch)."""
+        self._check(lib().lbm_set_schedule(self.ctx, SCHEDULE[schedule]))
+        return self
+
+    def stats(self):
+        """(steps advanced, step kernels launched) since the context was created."""
+        steps, launches = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(lib().lbm_stats(self.ctx, ctypes.byref(steps), ctypes.byref(launches)))
+        return steps.value, launches.value
+
+    def status(self):
+        """Synchronise the bound stream; raises LBMError on an asynchronous failure."""
+        self._check(lib().lbm_status(self.ctx))
         return self
 
     def strain_rate(self, formula=None, with_tau=False):
