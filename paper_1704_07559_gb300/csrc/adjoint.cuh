@@ -22,6 +22,7 @@
 #pragma once
 
 #include "step.cuh"
+#include "step_stream.cuh"
 
 namespace lbm {
 
@@ -252,6 +253,49 @@ __global__ void __launch_bounds__(128) k_adjoint_step(const AdjArgs<typename Sto
     node_backward<CLOSURE, true>(st, lam, Sb, R(0), a.st, mu, Fb);
     push(a, x, y, z, mu);
     for (int d = 0; d < 3; ++d) a.dF[d * N + node] += Fb[d];
+}
+
+// Several adjoint steps in one launch (the scheduler of step_stream.cuh): launch step k is the
+// reverse step of the state a0.st's source shifted by -k * c.ring elements (the states of a
+// checkpoint segment, equally spaced, visited backwards); lambda ping-pongs, a0 reading the first
+// lambda buffer and writing the second, a1 the reverse.  The nine-unit dependency covers the
+// push: step k writes lambda entries of the neighbouring units, which read their own entries of
+// step k - 1's output and wrote the buffer's previous contents.  lambda and the force-gradient
+// accumulator, which other blocks of the launch wrote, are read through L2; the states are
+// read-only for the whole launch.
+template <class ST, int CLOSURE>
+__device__ __forceinline__ void adjoint_unit(const AdjArgs<typename Store<ST>::R>& a, int z, int y0, int y1,
+                                             long long es) {
+    using R = typename Store<ST>::R;
+    const long long N = (long long)a.st.nx * a.st.ny * a.st.nz;
+    for (int y = y0; y < y1; ++y) {
+        for (int x = threadIdx.x; x < a.st.nx; x += blockDim.x) {
+            const int node = (z * a.st.ny + y) * a.st.nx + x;
+            R p[19], F[3], lam[19];
+            pull<D3Q19, ST>(a.st, x, y, z, p, es);
+            for (int d = 0; d < 3; ++d) F[d] = a.st.force_field[d * N + node];
+            sfor<19>([&](auto i) { lam[i] = __ldcg(a.lamp_in[CV(i)] + node); });
+            NodeFwd<R> st;
+            node_forward<CLOSURE>(p, F, a.st, st);
+            R mu[19], Fb[3];
+            const R Sb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+            node_backward<CLOSURE, true>(st, lam, Sb, R(0), a.st, mu, Fb);
+            push(a, x, y, z, mu);
+            for (int d = 0; d < 3; ++d) a.dF[d * N + node] = __ldcg(a.dF + d * N + node) + Fb[d];
+        }
+    }
+}
+
+template <class ST, int CLOSURE>
+__global__ void __launch_bounds__(128, 7) k_adjoint_stream(const AdjArgs<typename Store<ST>::R> a0,
+                                                        const AdjArgs<typename Store<ST>::R> a1, const StreamCtl c) {
+    stream_schedule(a0.st.ny, a0.st.nz, c, [&](int k, int z, int y0, int y1) {
+        const long long es = -(long long)k * c.ring;
+        if (k & 1)
+            adjoint_unit<ST, CLOSURE>(a1, z, y0, y1, es);
+        else
+            adjoint_unit<ST, CLOSURE>(a0, z, y0, y1, es);
+    });
 }
 
 // the functional at the final state: per-block FP64 partial sums of nu_eff S:S, the adjoint

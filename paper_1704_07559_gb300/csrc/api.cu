@@ -189,7 +189,7 @@ cudaError_t run_stream(lbm_ctx* c, int nsteps) {
     a1 = a0;
     set_buffers(c, &a0, c->buf[c->cur], c->buf[1 - c->cur]);
     set_buffers(c, &a1, c->buf[1 - c->cur], c->buf[c->cur]);
-    const lbm::StreamCtl ctl = {c->sync, nsteps, c->stream_rows, c->stream_tiles, stall ? 1 : 0};
+    const lbm::StreamCtl ctl = {c->sync, nsteps, c->stream_rows, c->stream_tiles, stall ? 1 : 0, 0};
     const int force = has_force(c) ? 1 : 0, forced = (stall || c->schedule == LBM_SCHEDULE_STREAM) ? 1 : 0;
     const int cl = c->p.closure, fm = c->p.formula;
     if (stall) c->schedule = LBM_SCHEDULE_AUTO;
@@ -409,16 +409,61 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
 
     // reverse sweep, segment by segment from the last, recomputing each segment's states
     int lc = 0;
+    const long long ring = (long long)(L.state / c->elem_bytes);  // elements between segment states
+    const int forced = c->schedule == LBM_SCHEDULE_STREAM ? 1 : 0;
     for (int sgi = L.ncp - 1; sgi >= 0; --sgi) {
-        const int k0 = sgi * seg, k1 = (k0 + seg < T) ? k0 + seg : T;
+        const int k0 = sgi * seg, k1 = (k0 + seg < T) ? k0 + seg : T, m = k1 - k0;
         const void* states[1024];
         states[0] = cp(sgi);
-        for (int i = 1; i < k1 - k0; ++i) {
+        for (int i = 1; i < m; ++i) states[i] = sg(i - 1);
+        // recompute the segment's states: the first from the checkpoint, the rest (FP32, where the
+        // schedule allows) in one ring launch that writes each step to the next state buffer
+        int i = 1;
+        if (m >= 2) {
+            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, states[0], sg(0));
+            if (e != cudaSuccess) return e;
+            i = 2;
+        }
+        if constexpr (!F64) {
+            if (m - 2 >= 2 && c->schedule != LBM_SCHEDULE_PER_STEP) {
+                lbm::StepArgs<float> ra;
+                fill_args(c, &ra);
+                ra.readout = 0;
+                ra.S_out = ra.tau_out = ra.drho_out = ra.u_out = nullptr;
+                set_buffers(c, &ra, sg(0), sg(1));
+                const lbm::StreamCtl ctl = {c->sync, m - 2, c->stream_rows, c->stream_tiles, 0, ring};
+                e = lbm::stream_ring_d3q19_f32(ra, ctl, c->p.closure, c->p.formula, has_force(c) ? 1 : 0, forced, s);
+                if (e == cudaSuccess)
+                    i = m;
+                else if (e != cudaErrorNotSupported)
+                    return e;
+            }
+        }
+        for (; i < m; ++i) {
             e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, states[i - 1], sg(i - 1));
             if (e != cudaSuccess) return e;
-            states[i] = sg(i - 1);
         }
-        for (int n = k1 - 1; n >= k0; --n) {
+        // reverse steps k1 - 1 .. k0 + 1 (states sg(m - 2) down to sg(0), equally spaced) in one
+        // launch where the schedule allows, the rest one launch per step
+        int n = k1 - 1;
+        if constexpr (!F64) {
+            if (m - 1 >= 2 && c->schedule != LBM_SCHEDULE_PER_STEP) {
+                lbm::AdjArgs<R> b0 = a, b1 = a;
+                set_buffers(c, &b0.st, states[m - 1], nullptr);
+                set_buffers(c, &b1.st, states[m - 1], nullptr);
+                lbm::set_lambda(&b0, static_cast<const R*>(lam[lc]), lam[1 - lc]);
+                lbm::set_lambda(&b1, static_cast<const R*>(lam[1 - lc]), lam[lc]);
+                const lbm::StreamCtl ctl = {c->sync, m - 1, c->stream_rows, c->stream_tiles, 0, ring};
+                e = lbm::adj_stream_f32(b0, b1, ctl, c->p.closure, forced, s);
+                if (e == cudaSuccess) {
+                    n = k0;
+                    if ((m - 1) & 1) lc = 1 - lc;
+                } else if (e != cudaErrorNotSupported) {
+                    return e;
+                }
+            }
+        }
+        for (; n >= k0; --n) {
             set_buffers(c, &a.st, states[n - k0], nullptr);
             lbm::set_lambda(&a, static_cast<const R*>(lam[lc]), lam[1 - lc]);
             if constexpr (F64)

@@ -26,6 +26,32 @@ static cudaError_t step_impl(const AdjArgs<typename Store<ST>::R>& a, int closur
     return launch_pdl(k_adjoint_step<ST, CL_NEWTON>, g, b, s, a);
 }
 
+// several adjoint steps per launch, with the forward multi-step launch's policy: lattices up to
+// 2^23 nodes with enough units that no block waits, unless forced
+template <int CLOSURE>
+static cudaError_t stream_impl(const AdjArgs<float>& a0, const AdjArgs<float>& a1, const StreamCtl& c,
+                               bool force_stream, cudaStream_t s) {
+    const long long N = (long long)a0.st.nx * a0.st.ny * a0.st.nz;
+    if (!force_stream && N > (1LL << 23)) return cudaErrorNotSupported;
+    static const int resident = resident_blocks(k_adjoint_stream<float, CLOSURE>);
+    StreamCtl u;
+    if (!pick_units(c, a0.st.ny, a0.st.nz, resident, &u) && !force_stream) return cudaErrorNotSupported;
+    const long long total = (long long)a0.st.nz * u.tiles_y * u.steps;
+    if (total >= (1LL << 31) || u.steps < 1) return cudaErrorInvalidValue;
+    const int grid = (int)(total < resident ? total : resident);
+    cudaError_t e = cudaMemsetAsync(u.sync + 1, 0, sizeof(int) * (1 + (size_t)a0.st.nz * u.tiles_y), s);
+    if (e != cudaSuccess) return e;
+    k_adjoint_stream<float, CLOSURE><<<grid, 128, 0, s>>>(a0, a1, u);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_stream_f32(const AdjArgs<float>& a0, const AdjArgs<float>& a1, const StreamCtl& c, int closure,
+                           int force_stream, cudaStream_t s) {
+    if (closure == CL_SMAG) return stream_impl<CL_SMAG>(a0, a1, c, force_stream != 0, s);
+    if (closure == CL_NEWTON) return stream_impl<CL_NEWTON>(a0, a1, c, force_stream != 0, s);
+    return cudaErrorNotSupported;
+}
+
 template <class R>
 static cudaError_t fold_impl(R* dF, double* dLdg, double rho0, long long n, cudaStream_t s) {
     k_fold<R><<<4 * 152, 256, 0, s>>>(dF, dLdg, rho0, n);

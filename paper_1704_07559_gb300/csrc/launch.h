@@ -45,6 +45,7 @@ struct StreamCtl {
     int rows;        // lattice rows (y) per unit (the launcher may take a multiple)
     int tiles_y;     // units per z plane: ceil(ny / rows)
     int first_step;  // 0; 1 only for the diagnostic that makes every dependency wait run out
+    long long ring;  // 0: two buffers; else step k's buffers are the first ones shifted by k * ring elements
 };
 
 constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in scratch
@@ -66,6 +67,9 @@ LBM_DECLARE_STREAM_ENTRY(d3q15_f16, float)
 LBM_DECLARE_STREAM_ENTRY(d3q15_bf16, float)
 LBM_DECLARE_STREAM_ENTRY(d2q9_f32, float)
 #undef LBM_DECLARE_STREAM_ENTRY
+// ring launches (each step writes a buffer of its own): D3Q19 FP32, Newtonian and Smagorinsky
+cudaError_t stream_ring_d3q19_f32(const StepArgs<float>& a, const StreamCtl& c, int closure, int formula, int force,
+                                  int force_stream, cudaStream_t s);
 
 LBM_DECLARE_ENTRY(d3q19_f64, double)
 LBM_DECLARE_ENTRY(d3q19_f32, float)

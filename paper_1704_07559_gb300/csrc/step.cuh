@@ -967,7 +967,8 @@ __device__ __forceinline__ F2 ldp2(const ST* p) {
 }
 
 template <class L, class ST, bool COH = false, class RS>
-__device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
+__device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q],
+                                             long long es = 0) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int node = (z * ny + y) * nx + x;
     const int dims[3] = {nx, ny, nz};
@@ -991,9 +992,9 @@ __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y
             }
         });
         if (nout == 0) {
-            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + (s[2] * ny + s[1]) * nx + s[0]);
+            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + es + ((s[2] * ny + s[1]) * nx + s[0]));
         } else {
-            RS v = ldp<COH>(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + node);
+            RS v = ldp<COH>(static_cast<const ST*>(a.srcp[opp<L>(CV(i))]) + es + node);
             if (nout == 1 && ((a.lid_mask >> face) & 1)) {
                 const RS cu = RS(L::c(CV(i), 0)) * a.lid[face][0] + RS(L::c(CV(i), 1)) * a.lid[face][1] +
                               RS(L::c(CV(i), 2)) * a.lid[face][2];
@@ -1005,7 +1006,7 @@ __device__ __forceinline__ void pull_general(const StepArgs<RS>& a, int x, int y
 }
 
 template <class L, class ST, bool COH = false, class RS>
-__device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q]) {
+__device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z, RS (&f)[L::Q], long long es = 0) {
     const int nx = a.nx, nxy = a.nx * a.ny;
     const int node = z * nxy + y * nx + x;
     const int dxm = x == 0 ? nx - 1 : -1;      // source of c_x = +1: x - 1 (wrapped)
@@ -1014,7 +1015,7 @@ __device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z,
         sfor<L::Q>([&](auto i) {
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
             const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) - (cy * nx + cz * nxy);
-            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + off);
+            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + es + off);
         });
         return;
     }
@@ -1023,11 +1024,11 @@ __device__ __forceinline__ void pull(const StepArgs<RS>& a, int x, int y, int z,
         sfor<L::Q>([&](auto i) {
             constexpr int cx = L::c(CV(i), 0), cy = L::c(CV(i), 1), cz = L::c(CV(i), 2);
             const int off = node + (cx > 0 ? dxm : (cx < 0 ? dxp : 0)) + w.template off<cy, cz>();
-            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + off);
+            f[i] = ldp<COH>(static_cast<const ST*>(a.srcp[CV(i)]) + es + off);
         });
         return;
     }
-    pull_general<L, ST, COH>(a, x, y, z, f);
+    pull_general<L, ST, COH>(a, x, y, z, f, es);
 }
 
 // Two nodes (x0, x0 + 1), x0 even, nx even: populations with c_x = 0 come as one aligned pair,
@@ -1090,11 +1091,13 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 
 // Everything of a step after the pull, for the node(s) starting at `node`: moments, strain rate
 // by the chosen route, closure, relaxation, force, and either the store of f* or (readout) the
-// store of S, tau, drho and u.
+// store of S, tau, drho and u.  ds shifts the populations' destination by that many elements (a
+// launch that writes each step to its own buffer of a ring); the pull's es does the same for the
+// source.
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
 __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>& a,
                                           std::conditional_t<VW == 2, F2, typename Store<ST>::R> (&f)[L::Q],
-                                          int node) {
+                                          int node, long long ds = 0) {
     using RS = typename Store<ST>::R;
     using R = std::conditional_t<VW == 2, F2, RS>;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
@@ -1285,7 +1288,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     }
 
     sfor<Q>([&](auto i) {
-        ST* p = static_cast<ST*>(a.dstp[CV(i)]) + node;
+        ST* p = static_cast<ST*>(a.dstp[CV(i)]) + ds + node;
         if constexpr (VW == 2)
             Store<ST>::st2(p, f[i] - out[i]);
         else

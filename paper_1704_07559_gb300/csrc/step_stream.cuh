@@ -66,9 +66,11 @@ __device__ __noinline__ static bool wait_count(const int* flag, int want, int* e
 }
 
 // One unit: rows [y0, y1) of plane z, one node per thread (PAIR false) or two x-adjacent nodes
-// per thread sharing the pull (PAIR true, nx even).
+// per thread sharing the pull (PAIR true, nx even).  es / ds shift the source / destination
+// populations by that many elements (ring launches; one node per thread only).
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, bool PAIR>
-__device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R>& a, int z, int y0, int y1) {
+__device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R>& a, int z, int y0, int y1,
+                                            long long es = 0, long long ds = 0) {
     using R = typename Store<ST>::R;
     for (int y = y0; y < y1; ++y) {
         if constexpr (PAIR) {
@@ -85,22 +87,23 @@ __device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R
         } else {
             for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
                 R f[L::Q];
-                pull<L, ST, true>(a, x, y, z, f);
-                step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, (z * a.ny + y) * a.nx + x);
+                pull<L, ST, true>(a, x, y, z, f, es);
+                step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, (z * a.ny + y) * a.nx + x, ds);
             }
         }
     }
 }
 
-// a0 reads buffer A and writes B (even steps of the launch), a1 the reverse (odd steps).
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, bool PAIR>
-__device__ __forceinline__ void stream_steps(const StepArgs<typename Store<ST>::R>& a0,
-                                             const StepArgs<typename Store<ST>::R>& a1, const StreamCtl& c) {
+// The scheduler: takes tickets until the launch's steps are exhausted and calls run(k, z, y0, y1)
+// for step k (0-based within the launch) of unit (z, band) once its neighbours have finished step
+// k - 1.  Every thread of the block calls it; run must not synchronise the block.
+template <class Run>
+__device__ __forceinline__ void stream_schedule(int ny, int nz, const StreamCtl& c, Run&& run) {
     __shared__ int s_ticket, s_skip;
     int* const err = c.sync;
     int* const ticket = c.sync + 1;
     int* const done = c.sync + 2;
-    const int nz = a0.nz, tiles = c.tiles_y, units = nz * tiles;
+    const int tiles = c.tiles_y, units = nz * tiles;
     const int total = c.steps * units;  // the host keeps it below 2^31
     for (;;) {
         // (the previous unit's last barrier orders these writes after every read of them)
@@ -126,15 +129,26 @@ __device__ __forceinline__ void stream_steps(const StepArgs<typename Store<ST>::
         }
         __syncthreads();
         if (!s_skip) {
-            const int y0 = ty * c.rows, y1 = min(a0.ny, y0 + c.rows);
-            if (k & 1)
-                stream_unit<L, ST, CLOSURE, FORMULA, FORCE, PAIR>(a1, z, y0, y1);
-            else
-                stream_unit<L, ST, CLOSURE, FORMULA, FORCE, PAIR>(a0, z, y0, y1);
+            const int y0 = ty * c.rows, y1 = min(ny, y0 + c.rows);
+            run(k, z, y0, y1);
         }
         __syncthreads();
         if (threadIdx.x == 0) st_release(done + z * tiles + ty, k + 1);
     }
+}
+
+// Two-buffer launches: a0 reads buffer A and writes B (even steps of the launch), a1 the reverse
+// (odd steps).  Ring launches (c.ring != 0): step k reads a0's source and writes a0's
+// destination, both shifted by k * c.ring elements (each step writes a buffer of its own).
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, bool PAIR>
+__device__ __forceinline__ void stream_steps(const StepArgs<typename Store<ST>::R>& a0,
+                                             const StepArgs<typename Store<ST>::R>& a1, const StreamCtl& c) {
+    stream_schedule(a0.ny, a0.nz, c, [&](int k, int z, int y0, int y1) {
+        if (k & 1)
+            stream_unit<L, ST, CLOSURE, FORMULA, FORCE, PAIR>(a1, z, y0, y1);
+        else
+            stream_unit<L, ST, CLOSURE, FORMULA, FORCE, PAIR>(a0, z, y0, y1);
+    });
 }
 
 // One node per thread, bound to the resident blocks of the one-step kernel (8 for the Yu route,
@@ -153,6 +167,16 @@ __global__ void __launch_bounds__(128, 7) k_step_stream_pair(const StepArgs<type
                                                              const StepArgs<typename Store<ST>::R> a1,
                                                              const StreamCtl c) {
     stream_steps<L, ST, CLOSURE, FORMULA, FORCE, true>(a0, a1, c);
+}
+
+// Ring launch (see stream_steps), one node per thread.
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__global__ void __launch_bounds__(128, FORMULA == F_YU ? 8 : 7)
+    k_step_stream_ring(const StepArgs<typename Store<ST>::R> a, const StreamCtl c) {
+    stream_schedule(a.ny, a.nz, c, [&](int k, int z, int y0, int y1) {
+        const long long sh = k * c.ring;
+        stream_unit<L, ST, CLOSURE, FORMULA, FORCE, false>(a, z, y0, y1, sh, sh);
+    });
 }
 
 template <class K>
@@ -219,6 +243,23 @@ cudaError_t launch_stream_form(const StepArgs<typename Store<ST>::R>& a0, const 
     return cudaGetLastError();
 }
 
+template <class L, class ST, int C, int F, bool FO>
+cudaError_t launch_stream_ring_form(const StepArgs<typename Store<ST>::R>& a, const StreamCtl& c, bool force_stream,
+                                    cudaStream_t s) {
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    if (!force_stream && N > (1LL << 23)) return cudaErrorNotSupported;
+    static const int resident = resident_blocks(k_step_stream_ring<L, ST, C, F, FO>);
+    StreamCtl u;
+    if (!pick_units(c, a.ny, a.nz, resident, &u) && !force_stream) return cudaErrorNotSupported;
+    const long long total = (long long)a.nz * u.tiles_y * u.steps;
+    if (total >= (1LL << 31) || u.steps < 1) return cudaErrorInvalidValue;
+    const int grid = (int)(total < resident ? total : resident);
+    cudaError_t e = cudaMemsetAsync(u.sync + 1, 0, sizeof(int) * (1 + (size_t)a.nz * u.tiles_y), s);
+    if (e != cudaSuccess) return e;
+    k_step_stream_ring<L, ST, C, F, FO><<<grid, 128, 0, s>>>(a, u);
+    return cudaGetLastError();
+}
+
 template <class L, class ST, int C, int F>
 cudaError_t launch_stream_cf(const StepArgs<typename Store<ST>::R>& a0, const StepArgs<typename Store<ST>::R>& a1,
                              const StreamCtl& c, int force, bool force_stream, cudaStream_t s) {
@@ -256,6 +297,30 @@ cudaError_t launch_stream(const StepArgs<typename Store<ST>::R>& a0, const StepA
 }
 
 }  // namespace lbm
+
+#define LBM_DEFINE_STREAM_RING_ENTRY(TAG, L, ST)                                                              \
+    namespace lbm {                                                                                          \
+    cudaError_t stream_ring_##TAG(const StepArgs<Store<ST>::R>& a, const StreamCtl& c, int closure,          \
+                                  int formula, int force, int force_stream, cudaStream_t s) {                \
+        const bool fs = force_stream != 0;                                                                   \
+        const bool yu = formula == F_YU;                                                                     \
+        if (closure == CL_SMAG) {                                                                            \
+            if (yu)                                                                                          \
+                return force ? launch_stream_ring_form<L, ST, CL_SMAG, F_YU, true>(a, c, fs, s)              \
+                             : launch_stream_ring_form<L, ST, CL_SMAG, F_YU, false>(a, c, fs, s);            \
+            return force ? launch_stream_ring_form<L, ST, CL_SMAG, F_CHAI, true>(a, c, fs, s)                \
+                         : launch_stream_ring_form<L, ST, CL_SMAG, F_CHAI, false>(a, c, fs, s);              \
+        }                                                                                                    \
+        if (closure == CL_NEWTON) {                                                                          \
+            if (yu)                                                                                          \
+                return force ? launch_stream_ring_form<L, ST, CL_NEWTON, F_YU, true>(a, c, fs, s)            \
+                             : launch_stream_ring_form<L, ST, CL_NEWTON, F_YU, false>(a, c, fs, s);          \
+            return force ? launch_stream_ring_form<L, ST, CL_NEWTON, F_CHAI, true>(a, c, fs, s)              \
+                         : launch_stream_ring_form<L, ST, CL_NEWTON, F_CHAI, false>(a, c, fs, s);            \
+        }                                                                                                    \
+        return cudaErrorNotSupported;                                                                        \
+    }                                                                                                        \
+    }
 
 #define LBM_DEFINE_STREAM_ENTRY(TAG, L, ST, EXTRA_CLOSURES)                                                  \
     namespace lbm {                                                                                          \
