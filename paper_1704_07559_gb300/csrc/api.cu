@@ -172,13 +172,12 @@ Tag tag_of(int q, int precision) {
     return T_NONE;
 }
 
-// Several steps in one launch (float storage; the lagged closure keeps per-node state outside
-// the populations and steps one launch at a time).  Returns cudaErrorNotSupported when the
+// Several steps in one launch (float storage).  Returns cudaErrorNotSupported when the
 // streamed form does not apply or (automatic schedule) is not expected to pay: more than 2^23
 // nodes, or too few units to keep every resident block busy without waiting; the caller then
 // launches step by step.
 cudaError_t run_stream(lbm_ctx* c, int nsteps) {
-    if (c->p.precision == LBM_FP64 || c->p.closure == LBM_SMAG_LAGGED || c->schedule == LBM_SCHEDULE_PER_STEP)
+    if (c->p.precision == LBM_FP64 || c->schedule == LBM_SCHEDULE_PER_STEP)
         return cudaErrorNotSupported;
     // the stall check starts at step 1 of the launch: the neighbours' step 0 never runs
     const bool stall = c->schedule == LBM_SCHEDULE_STALL_CHECK;

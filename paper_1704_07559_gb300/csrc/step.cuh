@@ -819,20 +819,21 @@ __device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepAr
     return tau;
 }
 
-// A per-node field value loaded with an asm volatile ld (its issue point stays where it is written)
+// A per-node field value loaded with an asm volatile ld (its issue point stays where it is written),
+// through L2: in a multi-step launch the value may have been written by another block
 template <class R, class RS>
 __device__ __forceinline__ R load_early(const RS* p) {
     if constexpr (std::is_same<R, F2>::value) {
         float2 v;
-        asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+        asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
         return F2(v);
     } else if constexpr (std::is_same<RS, double>::value) {
         double v;
-        asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
         return v;
     } else {
         float v;
-        asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return v;
     }
 }

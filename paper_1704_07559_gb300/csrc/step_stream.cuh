@@ -189,14 +189,16 @@ int resident_blocks(K kernel) {
 }
 
 // Unit height: c.rows (about 1024 nodes) times the largest m in {4, 2, 1} that still leaves more
-// units than resident blocks plus the span of units the first unit of a step waits for (three
-// y bands and three planes), so that no block waits; false when even m = 1 does not.
+// units than resident blocks plus the span of positions a unit's dependencies reach ahead of it
+// (two planes of bands and two bands; no planes when nz = 1), so that no block waits; false when
+// even m = 1 does not.
 inline bool pick_units(const StreamCtl& base, int ny, int nz, int resident, StreamCtl* out) {
     for (int m = 4; m >= 1; m /= 2) {
         const int rows = base.rows * m < ny ? base.rows * m : ny;
         const int tiles = (ny + rows - 1) / rows;
         const long long units = (long long)nz * tiles;
-        if (units >= resident + 3LL * tiles + 3) {
+        const long long span = (nz > 1 ? 2LL * tiles : 0) + 3;
+        if (units >= resident + span) {
             *out = base;
             out->rows = rows;
             out->tiles_y = tiles;
@@ -267,8 +269,7 @@ cudaError_t launch_stream_cf(const StepArgs<typename Store<ST>::R>& a0, const St
                  : launch_stream_form<L, ST, C, F, false>(a0, a1, c, force_stream, s);
 }
 
-// Closures with per-node state outside the populations (the lagged closure's tau field) stay
-// step by step; FP64 too (its arithmetic, not the step boundaries, bounds it).
+// FP64 stays step by step (its arithmetic, not the step boundaries, bounds it).
 template <class L, class ST, bool EXTRA_CLOSURES>
 cudaError_t launch_stream(const StepArgs<typename Store<ST>::R>& a0, const StepArgs<typename Store<ST>::R>& a1,
                           const StreamCtl& c, int closure, int formula, int force, bool force_stream,
@@ -290,6 +291,11 @@ cudaError_t launch_stream(const StepArgs<typename Store<ST>::R>& a0, const StepA
             if constexpr (EXTRA_CLOSURES)
                 return yu ? launch_stream_cf<L, ST, CL_SMAG_DEV, F_YU>(a0, a1, c, force, force_stream, s)
                           : launch_stream_cf<L, ST, CL_SMAG_DEV, F_CHAI>(a0, a1, c, force, force_stream, s);
+            return cudaErrorNotSupported;
+        case CL_SMAG_LAGGED:  // the stored tau is the node's own: its unit's previous step wrote it
+            if constexpr (EXTRA_CLOSURES)
+                return yu ? launch_stream_cf<L, ST, CL_SMAG_LAGGED, F_YU>(a0, a1, c, force, force_stream, s)
+                          : launch_stream_cf<L, ST, CL_SMAG_LAGGED, F_CHAI>(a0, a1, c, force, force_stream, s);
             return cudaErrorNotSupported;
         default:
             return cudaErrorNotSupported;

@@ -97,20 +97,36 @@ def test_auto_schedule_on_the_channel_equals_per_step():
         lat.close()
 
 
-def test_lagged_closure_and_fp64_keep_one_launch_per_step():
-    """The forms the streamed launch leaves out still step under a forced streamed schedule."""
-    for precision, closure in (("fp64", "smag"), ("fp32", "smag_lagged")):
-        c = make(19, (300, 20, 6), precision, closure, "yu", {})
-        c.lat.init(c.drho, c.u, c.g)
-        f0 = c.lat.get_state().clone()
-        t0 = None if c.lat.tau is None else c.lat.tau.clone()
-        c.lat.set_schedule("per_step").step(4)
-        ref = c.lat.get_state().clone()
-        c.lat.set_state(f0)
-        if t0 is not None:
-            c.lat.tau.copy_(t0)
-        c.lat.set_schedule("stream").step(4).status()
-        assert torch.equal(c.lat.get_state(), ref)
+def test_fp64_keeps_one_launch_per_step():
+    """FP64 (arithmetic-bound) steps one launch per step even under a forced streamed schedule."""
+    c = make(19, (300, 20, 6), "fp64", "smag", "yu", {})
+    c.lat.init(c.drho, c.u, c.g)
+    f0 = c.lat.get_state().clone()
+    c.lat.set_schedule("per_step").step(4)
+    ref = c.lat.get_state().clone()
+    c.lat.set_state(f0)
+    steps0, launches0 = c.lat.stats()
+    c.lat.set_schedule("stream").step(4).status()
+    steps1, launches1 = c.lat.stats()
+    assert (steps1 - steps0, launches1 - launches0) == (4, 4)
+    assert torch.equal(c.lat.get_state(), ref)
+
+
+@pytest.mark.parametrize("formula", ["yu", "chai"])
+def test_lagged_closure_streamed_equals_per_step(formula):
+    """The lagged closure's stored tau is read and rewritten by the node's own unit, one step after
+    another (possibly on different SMs): populations and the tau field after 7 streamed steps equal
+    7 one-step launches bit for bit."""
+    c = make(19, (300, 20, 6), "fp32", "smag_lagged", formula, dict(bc=WALL_Y, force=[1e-5, 0, 0]))
+    c.lat.init(c.drho, c.u, c.g)
+    f0, t0 = c.lat.get_state().clone(), c.lat.tau.clone()
+    c.lat.set_schedule("per_step").step(7)
+    ref, tref = c.lat.get_state().clone(), c.lat.tau.clone()
+    c.lat.set_state(f0)
+    c.lat.tau.copy_(t0)
+    c.lat.set_schedule("stream").step(7).status()
+    assert torch.equal(c.lat.get_state().view(torch.int32), ref.view(torch.int32))
+    assert torch.equal(c.lat.tau.view(torch.int32), tref.view(torch.int32))
 
 
 def test_a_dependency_wait_that_runs_out_is_reported():
