@@ -2,10 +2,13 @@
 strain rate (Yu's or Chai's formula), FP32 populations, on a 256 x 128 x 128 channel with
 halfway bounce-back walls at the y faces and a uniform body force g_x = 1e-6.
 
-One benchmark step is one lattice time step over the whole grid (one kernel launch: pull-stream,
-moments, strain rate, closure, relaxation, force, store).  The metric is MLUPS (million lattice
-node updates per second) and the fraction of the measured HBM bandwidth that the minimum
-traffic (19 populations read + 19 written, 152 bytes per node update) represents.
+One benchmark step is one lattice time step over the whole grid (pull-stream, moments, strain
+rate, closure, relaxation, force, store, all in one kernel).  The timed region is one
+lbm_step(K) call, which the library's automatic schedule runs as a single multi-step launch on
+this lattice (steps overlap tile by tile instead of draining the GPU between them).  The metric
+is MLUPS (million lattice node updates per second) and the fraction of the measured HBM bandwidth
+that the minimum traffic (19 populations read + 19 written, 152 bytes per node update)
+represents.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|fp16s|bf16s|fp64] [--formula yu|chai] [--lattice 19|15]
