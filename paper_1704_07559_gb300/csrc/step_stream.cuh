@@ -151,10 +151,17 @@ __device__ __forceinline__ void stream_steps(const StepArgs<typename Store<ST>::
     });
 }
 
-// One node per thread, bound to the resident blocks of the one-step kernel (8 for the Yu route,
-// 64 registers; 7 for Chai, 72): unbounded, the unit loop costs 7-8 more registers and a block.
+// One node per thread, 8 resident blocks (64 registers) for the Yu route and for Chai with the
+// Smagorinsky and power-law closures (Chai: 24 B of spills, measured 4.5% faster than 7 blocks at
+// 72 registers on the channel), 7 for the other Chai forms (spills of 64-144 B at 64 registers).
+// Unbounded, the unit loop costs 7-8 more registers and a block.
+template <int CLOSURE, int FORMULA>
+constexpr int stream_min_blocks() {
+    return (FORMULA == F_YU || CLOSURE == CL_SMAG || CLOSURE == CL_POWERLAW) ? 8 : 7;
+}
+
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128, FORMULA == F_YU ? 8 : 7)
+__global__ void __launch_bounds__(128, stream_min_blocks<CLOSURE, FORMULA>())
     k_step_stream(const StepArgs<typename Store<ST>::R> a0, const StepArgs<typename Store<ST>::R> a1,
                   const StreamCtl c) {
     stream_steps<L, ST, CLOSURE, FORMULA, FORCE, false>(a0, a1, c);
