@@ -185,9 +185,10 @@ int lbm_step(lbm_ctx* ctx, int n);
  *                         ahead, so that every dependency wait runs out (about two seconds);
  *                         the launch ends, lbm_status then reports LBM_ERR_STATE, the state is
  *                         invalid and the schedule is back to LBM_SCHEDULE_AUTO.
- * A launch of several steps cuts the lattice into units (one z plane by a band of y rows, all of
- * x); a unit runs step k once its neighbouring units (z +-1, band +-1, periodically wrapped) have
- * completed step k-1, so consecutive steps overlap instead of draining the GPU between them.
+ * A launch of several steps (at most 4096; lbm_step(n) makes as many launches as it needs) cuts
+ * the lattice into units (one z plane by a band of y rows, all of x); a unit runs step k once its
+ * neighbouring units (z +-1, band +-1, periodically wrapped) have completed step k-1, so
+ * consecutive steps overlap instead of draining the GPU between them.
  * Errors: LBM_ERR_ARG for an unknown schedule. */
 #define LBM_SCHEDULE_AUTO 0
 #define LBM_SCHEDULE_PER_STEP 1

@@ -260,13 +260,16 @@ cudaError_t run_step(lbm_ctx* c, int formula, int readout, void* S, void* tau, v
 }
 
 // n steps from the current buffer (which alternates): several per launch where the schedule
-// allows (in chunks that keep the ticket count below 2^31), one launch per step otherwise.
+// allows, one launch per step otherwise.  A multi-step launch runs at most STREAM_CHUNK steps
+// (and keeps its ticket count below 2^31), so that no single kernel runs for minutes.
 // *launches counts the step kernels launched.
+constexpr int STREAM_CHUNK = 4096;
+
 cudaError_t advance(lbm_ctx* c, int n, long long* launches) {
     int it = 0;
     if (n >= 2) {
         const long long units = (long long)c->nz * c->stream_tiles;
-        const int chunk = (int)std::min<long long>(n, 0x7fffffffLL / units);
+        const int chunk = (int)std::min<long long>(std::min(n, STREAM_CHUNK), 0x7fffffffLL / units);
         while (n - it >= 2 && chunk >= 2) {
             const int k = std::min(chunk, n - it);
             cudaError_t e = run_stream(c, k);
