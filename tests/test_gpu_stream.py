@@ -175,3 +175,18 @@ def test_adjoint_under_the_streamed_schedule_equals_per_step(seg):
     assert out["per_step"][0] == out["stream"][0]
     assert torch.equal(out["per_step"][1], out["stream"][1])
     assert torch.equal(out["per_step"][2].view(torch.int32), out["stream"][2].view(torch.int32))
+
+
+def test_long_runs_are_split_into_launches_of_at_most_4096_steps():
+    """lbm_step(5000) under the streamed schedule makes two multi-step launches (4096 + 904) and
+    equals 5000 one-step launches bit for bit."""
+    c = make(19, (300, 20, 6), "fp32", "smag", "yu", dict(force=[1e-6, 0, 0]))
+    c.lat.init(c.drho, c.u, c.g)
+    f0 = c.lat.get_state().clone()
+    ref = c.lat.set_schedule("per_step").step(5000).get_state().clone()
+    c.lat.set_state(f0)
+    steps0, launches0 = c.lat.stats()
+    got = c.lat.set_schedule("stream").step(5000).status().get_state()
+    steps1, launches1 = c.lat.stats()
+    assert (steps1 - steps0, launches1 - launches0) == (5000, 2)
+    assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
