@@ -190,3 +190,37 @@ def test_long_runs_are_split_into_launches_of_at_most_4096_steps():
     steps1, launches1 = c.lat.stats()
     assert (steps1 - steps0, launches1 - launches0) == (5000, 2)
     assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
+
+
+def test_two_multi_step_launches_running_concurrently():
+    """Two contexts on two streams, each running 200 steps as one multi-step launch at the same
+    time (their blocks share the SMs; neither launch is cooperative): both end bit-identical to
+    one launch per step, with no wait running out."""
+    from paper_1704_07559_gb300 import inputs as I
+    from test_gpu_parity import rates
+
+    dims = [(256, 64, 64), (192, 48, 80)]
+    lats, refs = [], []
+    for k, (nx, ny, nz) in enumerate(dims):
+        st = torch.cuda.Stream()
+        lat = lbm.Lattice(19, nx, ny, nz, rates=rates(19, 0.55), precision="fp32", closure="smag", smag_cs=0.17,
+                          formula="yu" if k == 0 else "chai", force=[1e-6, 0, 0], stream=st)
+        drho, u = I.random_fourier(nx, ny, nz, kmax=3, rms=0.02, seed=10 + k)
+        lat.init(drho, u)
+        torch.cuda.synchronize()
+        f0 = lat.get_state().clone()
+        torch.cuda.synchronize()
+        lat.set_schedule("per_step").step(200)
+        torch.cuda.synchronize()
+        refs.append(lat.get_state().clone())
+        torch.cuda.synchronize()
+        lat.set_state(f0)
+        torch.cuda.synchronize()
+        lats.append(lat)
+    for lat in lats:  # both launches queued before either is waited for
+        lat.set_schedule("stream").step(200)
+    for lat, ref in zip(lats, refs):
+        lat.status()
+        got = lat.get_state()
+        torch.cuda.synchronize()
+        assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
