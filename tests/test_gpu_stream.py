@@ -207,13 +207,13 @@ def test_two_multi_step_launches_running_concurrently():
                           formula="yu" if k == 0 else "chai", force=[1e-6, 0, 0], stream=st)
         drho, u = I.random_fourier(nx, ny, nz, kmax=3, rms=0.02, seed=10 + k)
         lat.init(drho, u)
+        g = lat.get_state()  # copied on the lattice's stream
         torch.cuda.synchronize()
-        f0 = lat.get_state().clone()
-        torch.cuda.synchronize()
+        f0 = g.clone()
         lat.set_schedule("per_step").step(200)
+        g = lat.get_state()
         torch.cuda.synchronize()
-        refs.append(lat.get_state().clone())
-        torch.cuda.synchronize()
+        refs.append(g.clone())
         lat.set_state(f0)
         torch.cuda.synchronize()
         lats.append(lat)
