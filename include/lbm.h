@@ -172,11 +172,11 @@ int lbm_step(lbm_ctx* ctx, int n);
 
 /* How lbm_step(n >= 2) launches its steps.
  *  LBM_SCHEDULE_AUTO      several steps per launch when the storage is FP32/FP16S/BF16S, the
- *                         lattice has at most 2^23 nodes and
+ *                         lattice is 3D with at most 2^22 nodes and
  *                         more units (a z plane times a band of y rows of about 1024-4096 nodes)
  *                         than the GPU holds resident blocks; one launch per step otherwise (the
- *                         default).  On larger lattices a step boundary costs less than the
- *                         multi-step launch's synchronisation.
+ *                         default).  On larger lattices, and on D2Q9 lattices, a step boundary
+ *                         costs less than the multi-step launch's synchronisation.
  *  LBM_SCHEDULE_PER_STEP  one launch per step.
  *  LBM_SCHEDULE_STREAM    several steps per launch wherever the storage allows it (not FP64),
  *                         whatever the lattice size.
