@@ -173,9 +173,9 @@ Tag tag_of(int q, int precision) {
 }
 
 // Several steps in one launch (float storage).  Returns cudaErrorNotSupported when the
-// streamed form does not apply or (automatic schedule) is not expected to pay: more than 2^23
-// nodes, or too few units to keep every resident block busy without waiting; the caller then
-// launches step by step.
+// streamed form does not apply or (automatic schedule) is not expected to pay: a D2Q9 lattice,
+// more than 2^22 nodes, or too few units to keep every resident block busy without waiting; the
+// caller then launches step by step.
 cudaError_t run_stream(lbm_ctx* c, int nsteps) {
     if (c->p.precision == LBM_FP64 || c->schedule == LBM_SCHEDULE_PER_STEP)
         return cudaErrorNotSupported;
