@@ -113,3 +113,29 @@ def test_null_context_calls_fail_cleanly(L):
     assert L.lbm_bind_tau(None, None) == -1
     assert L.lbm_destroy(None) == 0
     assert L.lbm_layout(None, None, None, None) == -1
+    assert L.lbm_set_schedule(None, 0) == -1
+    assert L.lbm_status(None) == -1
+    assert L.lbm_stats(None, None, None) == -1
+
+
+def header_constants(prefix):
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (%s\w+) (-?\d+)" % prefix, text, re.M)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's name tables carry the header's values (schedules, closures, precisions,
+    boundary kinds, formulas, error codes)."""
+    from paper_1704_07559_gb300 import lbm
+
+    sched = header_constants("LBM_SCHEDULE_")
+    assert {k: sched["LBM_SCHEDULE_" + k.upper()] for k in lbm.SCHEDULE} == lbm.SCHEDULE
+    cl = header_constants("LBM_")
+    assert lbm.CLOSURE == {"newton": cl["LBM_NEWTON"], "smag": cl["LBM_SMAG"], "powerlaw": cl["LBM_POWERLAW"],
+                           "smag_lagged": cl["LBM_SMAG_LAGGED"], "smag_dev": cl["LBM_SMAG_DEV"]}
+    assert lbm.PRECISION == {"fp64": cl["LBM_FP64"], "fp32": cl["LBM_FP32"], "fp16s": cl["LBM_FP16S"],
+                             "bf16s": cl["LBM_BF16S"]}
+    assert lbm.FORMULA == {"yu": cl["LBM_YU"], "chai": cl["LBM_CHAI"]}
+    assert lbm.BC == {"periodic": cl["LBM_PERIODIC"], "wall": cl["LBM_WALL"], "lid": cl["LBM_LID"]}
+    errs = header_constants("LBM_ERR_")
+    assert {v: k for k, v in errs.items()} == {k: v for k, v in lbm.ERRORS.items()}
