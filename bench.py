@@ -241,14 +241,34 @@ def job_rate(ms_local, updates_local, dist=None, device="cpu"):
     return ms_local, world * updates_local / (ms_local * 1e-3) / 1e6
 
 
+FMA_PROBE_SRC = os.path.join(ROOT, "bench_fma_peak.cu")
+FMA_PROBE_LIB = os.path.join(ROOT, "libbench_fma_peak.so")
+
+
+def build_fma_probe(force=False):
+    """Compile the benchmark's FMA-throughput probe (bench_fma_peak.cu, not part of the library)
+    for sm_103a if its source is newer than the shared object; return the object's path."""
+    if not force and os.path.exists(FMA_PROBE_LIB) and os.path.getmtime(FMA_PROBE_LIB) >= os.path.getmtime(FMA_PROBE_SRC):
+        return FMA_PROBE_LIB
+    import shutil
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    tmp = FMA_PROBE_LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC", "-shared", "-o", tmp,
+           FMA_PROBE_SRC, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed on %s:\n%s%s" % (FMA_PROBE_SRC, r.stdout, r.stderr))
+    os.replace(tmp, FMA_PROBE_LIB)
+    return FMA_PROBE_LIB
+
+
 def alu_peaks():
     """Measured FP32 and FP64 FMA throughput of this GPU (TFLOP/s, 2 flops per FMA), from the
-    benchmark's probe library: the arithmetic ceilings beside the HBM roofline."""
+    benchmark's probe: the arithmetic ceilings beside the HBM roofline."""
     import ctypes
 
-    from paper_1704_07559_gb300 import build
-
-    lib = ctypes.CDLL(build.build_probe())
+    lib = ctypes.CDLL(build_fma_probe())
     lib.fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     out = {}
     for name, fp64 in (("fp32_fma_tflops", 0), ("fp64_fma_tflops", 1)):

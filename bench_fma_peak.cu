@@ -1,4 +1,4 @@
-// fma_peak.cu -- measured FP32 and FP64 FMA throughput of the current GPU (libfmapeak.so).
+// bench_fma_peak.cu -- measured FP32 and FP64 FMA throughput of the current GPU (libbench_fma_peak.so, built by bench.py).
 //
 // A measurement probe for the benchmark, not part of the lattice Boltzmann library: it shows
 // where the FP32 and FP64 arithmetic ceilings lie relative to the step kernels, which are bound

@@ -62,24 +62,6 @@ def build(force=False, verbose=False, extra=()):
     return LIB
 
 
-PROBE_SRC = os.path.join(HERE, "probe", "fma_peak.cu")
-PROBE_LIB = os.path.join(HERE, "libfmapeak.so")
-
-
-def build_probe(force=False):
-    """Compile the FMA-throughput probe that the benchmark loads (libfmapeak.so, not part of the
-    library's C ABI) if its source is newer; return its path."""
-    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
-        return PROBE_LIB
-    tmp = PROBE_LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-O3", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, PROBE_SRC, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed on %s:\n%s%s" % (PROBE_SRC, r.stdout, r.stderr))
-    os.replace(tmp, PROBE_LIB)
-    return PROBE_LIB
-
-
 if __name__ == "__main__":
     import sys
     print(build(force=True, verbose="-v" in sys.argv, extra=["-Xptxas", "-v"] if "-v" in sys.argv else []))

@@ -4,89 +4,25 @@
 
 #include "launch.h"
 #include "step.cuh"
-#include "step_async.cuh"
 
 namespace lbm {
 
-// Step kernel selection for the float compute types (FP32, FP16S, BF16S):
-//   LBM_STEP_FORM 0: one node per thread, direct loads (k_step, VW = 1); for 16-bit storage with
-//                    nx even, k_step_pair_seq (form 6) instead;
-//   LBM_STEP_FORM 1: persistent double-buffered k_step_async, one node per thread;
-//   LBM_STEP_FORM 2: persistent double-buffered k_step_async, two nodes per thread in packed
-//                    FP32 pairs when nx is even (one node per thread otherwise);
-//   LBM_STEP_FORM 3: persistent k_step_prefetch (next node's loads in registers), one node;
-//   LBM_STEP_FORM 4: persistent k_step_prefetch, two nodes per thread when nx is even;
-//   LBM_STEP_FORM 5: k_step_pair, two nodes per thread in packed FP32 pairs when nx is even;
-//   LBM_STEP_FORM 6: k_step_pair_seq, two nodes per thread sharing the pull, collided one after
-//                    the other in scalar arithmetic, when nx is even.
-// FP64 always uses k_step (its arithmetic, not its loads, bounds it).
-#ifndef LBM_STEP_FORM
-#define LBM_STEP_FORM 0
-#endif
-
-template <class ST>
-constexpr bool float_compute() {
-    return std::is_same<typename Store<ST>::R, float>::value;
-}
-
-template <class L, class ST, int C, int F, bool FO, int VW, bool PREFETCH>
-cudaError_t launch_async(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
-    const int nseg = (a.nx + ASYNC_THREADS * VW - 1) / (ASYNC_THREADS * VW);
-    const long long tiles = (long long)nseg * a.ny * a.nz;
-    const int smem = PREFETCH ? 0 : 2 * L::Q * ASYNC_THREADS * slot_bytes<ST, VW>();
-    static int per_sm = 0, sms = 0;  // occupancy of this instantiation, found once
-    if (per_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (PREFETCH)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_prefetch<L, ST, C, F, FO, VW>, ASYNC_THREADS, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_async<L, ST, C, F, FO, VW>, ASYNC_THREADS, smem);
-        if (per_sm < 1) per_sm = 1;
-    }
-    const long long want = (long long)per_sm * sms;
-    const int grid = (int)(tiles < want ? tiles : want);
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if constexpr (PREFETCH)
-        k_step_prefetch<L, ST, C, F, FO, VW><<<grid, ASYNC_THREADS, 0, s>>>(a, nseg, (int)tiles);
-    else
-        k_step_async<L, ST, C, F, FO, VW><<<grid, ASYNC_THREADS, smem, s>>>(a, nseg, (int)tiles);
-    return cudaGetLastError();
-}
-
+// Step kernel selection: one node per thread (k_step), except 16-bit storage with nx even and no
+// read-out, which runs two x-adjacent nodes per thread sharing the pull (k_step_pair_seq; the
+// 16-bit step is issue-bound and the shared pull saves instructions; FP32 and FP64 measured
+// slower in that form and stay one node per thread).
 template <class L, class ST, int C, int F, bool FO>
 cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
-    // 16-bit storage (issue-bound): two nodes per thread sharing the pull when nx is even
-    // (measured 3-12% faster than one node per thread; slower for FP32, which stays one per thread)
-    if constexpr (sizeof(ST) == 2 && LBM_STEP_FORM == 0) {
+    if constexpr (sizeof(ST) == 2) {
         if (!a.readout && a.nx % 2 == 0) {
             dim3 g, b;
             lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
             return launch_pdl(k_step_pair_seq<L, ST, C, F, FO>, g, b, s, a);
         }
     }
-    if constexpr (float_compute<ST>() && LBM_STEP_FORM != 0) {
-        if (LBM_STEP_FORM == 5 && !a.readout && a.nx % 2 == 0) {
-            dim3 g, b;
-            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
-            return launch_pdl(k_step_pair<L, ST, C, F, FO>, g, b, s, a);
-        }
-        if (LBM_STEP_FORM == 6 && !a.readout && a.nx % 2 == 0) {
-            dim3 g, b;
-            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
-            return launch_pdl(k_step_pair_seq<L, ST, C, F, FO>, g, b, s, a);
-        }
-        if (LBM_STEP_FORM < 5 && !a.readout) {
-            constexpr bool PF = LBM_STEP_FORM >= 3;
-            constexpr bool PAIRS = LBM_STEP_FORM == 2 || LBM_STEP_FORM == 4;
-            if (PAIRS && a.nx % 2 == 0) return launch_async<L, ST, C, F, FO, 2, PF>(a, s);
-            return launch_async<L, ST, C, F, FO, 1, PF>(a, s);
-        }
-    }
     dim3 g, b;
     lattice_grid(a.nx, a.ny, a.nz, &g, &b);
-    return launch_pdl(k_step<L, ST, C, F, FO, 1>, g, b, s, a);
+    return launch_pdl(k_step<L, ST, C, F, FO>, g, b, s, a);
 }
 
 template <class L, class ST, int C, int F>

@@ -17,8 +17,8 @@
 // With a closure the viscous rates are unknown, so both routes split S = A + s_nu B (exact:
 // S is linear in the rates) and solve the scalar fixed point for tau = 1/s_nu.
 //
-// A thread owns VW x-adjacent nodes: VW = 1 (scalar R = float or double), or VW = 2 with R = F2,
-// the packed pair of vec2.cuh, so each arithmetic instruction advances both nodes.
+// A thread owns one node, or (16-bit storage) two x-adjacent nodes that share the pull's address
+// arithmetic and then collide one after the other.
 //
 // All lattice coefficients enter as compile-time constants: loops over populations and moments
 // are compile-time sequences (sfor) so each entry of T and c folds into an add, a subtract or
@@ -34,7 +34,6 @@
 #include <utility>
 
 #include "lattice.cuh"
-#include "vec2.cuh"
 
 namespace lbm {
 
@@ -53,6 +52,20 @@ __host__ __device__ __forceinline__ void sfor(F&& f) {
     sfor_impl(f, std::make_integer_sequence<int, N>{});
 }
 #define CV(x) (decltype(x)::value)
+
+// fused multiply-add under one name for both compute types
+__device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+
+// the populations of two x-adjacent nodes (a plain pair: the arithmetic is scalar)
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ __forceinline__ F2(float a, float b) : v{a, b} {}
+    __device__ __forceinline__ explicit F2(float2 u) : v(u) {}
+    __device__ __forceinline__ float lo() const { return v.x; }
+    __device__ __forceinline__ float hi() const { return v.y; }
+};
 
 // acc + t x for a compile-time integer t
 template <int T, class R>
@@ -80,7 +93,7 @@ __device__ __forceinline__ constexpr R cst(double c) {
 }
 
 // ------------------------------------------------------------------------------------------
-// storage types: scalar access, and the pair access of the two-node path.  ld/ld2 read through
+// storage types: scalar access, and the pair load of the two-node path.  ld/ld2 read through
 // the non-coherent path (the buffer is read-only for the whole kernel); ldc/ld2c read through L2
 // only (ld.global.cg), for a kernel that reads populations other blocks of the same kernel wrote
 // after synchronising with them.
@@ -103,7 +116,6 @@ struct Store<float> {
     // aligned pair p[0], p[1] (p 8-byte aligned)
     static __device__ __forceinline__ F2 ld2(const float* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
     static __device__ __forceinline__ F2 ld2c(const float* p) { return F2(__ldcg(reinterpret_cast<const float2*>(p))); }
-    static __device__ __forceinline__ void st2(float* p, F2 v) { __stcs(reinterpret_cast<float2*>(p), v.v); }
 };
 template <>
 struct Store<__half> {
@@ -117,9 +129,6 @@ struct Store<__half> {
     static __device__ __forceinline__ F2 ld2c(const __half* p) {
         return F2(__half22float2(__ldcg(reinterpret_cast<const __half2*>(p))));
     }
-    static __device__ __forceinline__ void st2(__half* p, F2 v) {
-        *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v);
-    }
 };
 template <>
 struct Store<__nv_bfloat16> {
@@ -132,9 +141,6 @@ struct Store<__nv_bfloat16> {
     }
     static __device__ __forceinline__ F2 ld2c(const __nv_bfloat16* p) {
         return F2(__bfloat1622float2(__ldcg(reinterpret_cast<const __nv_bfloat162*>(p))));
-    }
-    static __device__ __forceinline__ void st2(__nv_bfloat16* p, F2 v) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
     }
 };
 
@@ -758,23 +764,6 @@ __device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const
 // ------------------------------------------------------------------------------------------
 // closure: solve tau with S = A + (1/tau) B
 
-// per-node fields of the compute type (one node, or the aligned pair of the packed form)
-template <class R, class RS>
-__device__ __forceinline__ R load_field(const RS* p) {
-    if constexpr (std::is_same<R, F2>::value)
-        return F2(*reinterpret_cast<const float2*>(p));
-    else
-        return *p;
-}
-template <class R, class RS>
-__device__ __forceinline__ void store_field(RS* p, R v) {
-    if constexpr (std::is_same<R, F2>::value)
-        *reinterpret_cast<float2*>(p) = v.v;
-    else
-        *p = v;
-}
-
-
 template <class L, class R>
 __device__ __forceinline__ R strain_dot(const R (&S)[L::NS], const R (&T)[L::NS]) {
     // S:T with the off-diagonal components counted twice
@@ -821,13 +810,9 @@ __device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepAr
 
 // A per-node field value loaded with an asm volatile ld (its issue point stays where it is written),
 // through L2: in a multi-step launch the value may have been written by another block
-template <class R, class RS>
-__device__ __forceinline__ R load_early(const RS* p) {
-    if constexpr (std::is_same<R, F2>::value) {
-        float2 v;
-        asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-        return F2(v);
-    } else if constexpr (std::is_same<RS, double>::value) {
+template <class RS>
+__device__ __forceinline__ RS load_early(const RS* p) {
+    if constexpr (std::is_same<RS, double>::value) {
         double v;
         asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
         return v;
@@ -847,60 +832,31 @@ __device__ __forceinline__ RS tau_deviatoric(RS qc, const StepArgs<RS>& a) {
     return RS(0.5) * (a.tau0 + c_sqrt(fma(a.tau0, a.tau0, RS(4) * a.smag_c3 * b)));
 }
 
-// Returns tau, sets snu = 1/tau and S = A + snu B.  For the packed pair each node solves its own
-// fixed point.  The lagged closure collides with tau_prev, the tau stored at the (first) node
-// `node` (loaded by the caller together with the populations), and in a step (not a read-out)
-// stores tau0 + 3 Cs^2 |S| there for the next step.
+// Returns tau, sets snu = 1/tau and S = A + snu B.  The lagged closure collides with tau_prev, the
+// tau stored at `node` (loaded by the caller together with the populations), and in a step (not a
+// read-out) stores tau0 + 3 Cs^2 |S| there for the next step.
 template <class L, class R, int CLOSURE, class RS>
 __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS], const StepArgs<RS>& a,
                                        R (&S)[L::NS], R& snu, int node, R tau_prev = R(0.0f)) {
-    constexpr bool PAIR = std::is_same<R, F2>::value;
     if constexpr (CLOSURE == CL_NEWTON) {
         snu = R(a.s[L::NU0]);
         affine<L>(A, B, snu, S);
         return R(a.tau0);
     } else if constexpr (CLOSURE == CL_SMAG_LAGGED) {
         const R tau = tau_prev;
-        if constexpr (PAIR)
-            snu = F2(c_rcp(tau.lo()), c_rcp(tau.hi()));
-        else
-            snu = c_rcp(tau);
+        snu = c_rcp(tau);
         affine<L>(A, B, snu, S);
-        if (!a.readout) {
-            const R ss = strain_dot<L>(S, S);
-            R tn;
-            if constexpr (PAIR)
-                tn = F2(fma(a.smag_c3, c_sqrt(2.0f * ss.lo()), a.tau0), fma(a.smag_c3, c_sqrt(2.0f * ss.hi()), a.tau0));
-            else
-                tn = fma(a.smag_c3, c_sqrt(RS(2) * ss), a.tau0);
-            store_field(a.tau_field + node, tn);
-        }
+        if (!a.readout) a.tau_field[node] = fma(a.smag_c3, c_sqrt(RS(2) * strain_dot<L>(S, S)), a.tau0);
         return tau;
     } else if constexpr (CLOSURE == CL_SMAG_DEV) {
-        const R qc = strain_dot<L>(B, B);
-        R tau;
-        if constexpr (PAIR) {
-            const float t0 = tau_deviatoric(qc.lo(), a), t1 = tau_deviatoric(qc.hi(), a);
-            tau = F2(t0, t1);
-            snu = F2(c_rcp(t0), c_rcp(t1));
-        } else {
-            tau = tau_deviatoric(qc, a);
-            snu = c_rcp(tau);
-        }
+        const R tau = tau_deviatoric(strain_dot<L>(B, B), a);
+        snu = c_rcp(tau);
         affine<L>(A, B, snu, S);
         return tau;
     } else {
         const R qa = strain_dot<L>(A, A), qb2 = R(2.0f) * strain_dot<L>(A, B), qc = strain_dot<L>(B, B);
-        R tau;
-        if constexpr (std::is_same<R, F2>::value) {
-            const float t0 = tau_fixed_point<CLOSURE>(qa.lo(), qb2.lo(), qc.lo(), a);
-            const float t1 = tau_fixed_point<CLOSURE>(qa.hi(), qb2.hi(), qc.hi(), a);
-            tau = F2(t0, t1);
-            snu = F2(c_rcp(t0), c_rcp(t1));
-        } else {
-            tau = tau_fixed_point<CLOSURE>(qa, qb2, qc, a);
-            snu = c_rcp(tau);
-        }
+        const R tau = tau_fixed_point<CLOSURE>(qa, qb2, qc, a);
+        snu = c_rcp(tau);
         affine<L>(A, B, snu, S);
         return tau;
     }
@@ -1095,12 +1051,11 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 // store of S, tau, drho and u.  ds shifts the populations' destination by that many elements (a
 // launch that writes each step to its own buffer of a ring); the pull's es does the same for the
 // source.
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
-__device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>& a,
-                                          std::conditional_t<VW == 2, F2, typename Store<ST>::R> (&f)[L::Q],
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>& a, typename Store<ST>::R (&f)[L::Q],
                                           int node, long long ds = 0) {
     using RS = typename Store<ST>::R;
-    using R = std::conditional_t<VW == 2, F2, RS>;
+    using R = RS;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
     const long long N = (long long)a.nx * a.ny * a.nz;  // component offsets c*N exceed 2^31 on big grids
 
@@ -1112,7 +1067,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     R F[3] = {R(0.0f), R(0.0f), R(0.0f)};
     if constexpr (FORCE) {
         if (a.force_field) {
-            sfor<L::D>([&](auto d) { F[d] = load_field<R>(a.force_field + CV(d) * N + node); });
+            sfor<L::D>([&](auto d) { F[d] = a.force_field[CV(d) * N + node]; });
         } else {
             sfor<L::D>([&](auto d) { F[d] = R(a.F[d]); });
         }
@@ -1120,7 +1075,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     // the lagged closure's stored tau, loaded next to the populations so its latency overlaps theirs
     // (an asm volatile load keeps it there instead of next to its use after the moment arithmetic)
     R tau_prev = R(0.0f);
-    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_early<R>(a.tau_field + node);
+    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_early(a.tau_field + node);
     const R ir0 = R(a.inv_rho0);
     R drho, j[3] = {R(0.0f), R(0.0f), R(0.0f)}, u[3] = {R(0.0f), R(0.0f), R(0.0f)};
     R S[NS], tau, snu;
@@ -1289,63 +1244,36 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     }
 
     sfor<Q>([&](auto i) {
-        ST* p = static_cast<ST*>(a.dstp[CV(i)]) + ds + node;
-        if constexpr (VW == 2)
-            Store<ST>::st2(p, f[i] - out[i]);
-        else
-            Store<ST>::st(p, f[i] - out[i]);
+        Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + ds + node, f[i] - out[i]);
     });
     return;
 
 readout:
     if (a.S_out) {
 #pragma unroll
-        for (int c = 0; c < NS; ++c) store_field(a.S_out + c * N + node, S[c]);
+        for (int c = 0; c < NS; ++c) a.S_out[c * N + node] = S[c];
     }
-    if (a.tau_out) store_field(a.tau_out + node, tau);
-    if (a.drho_out) store_field(a.drho_out + node, drho);
+    if (a.tau_out) a.tau_out[node] = tau;
+    if (a.drho_out) a.drho_out[node] = drho;
     if (a.u_out) {
 #pragma unroll
-        for (int d = 0; d < L::D; ++d) store_field(a.u_out + d * N + node, u[d]);
+        for (int d = 0; d < L::D; ++d) a.u_out[d * N + node] = u[d];
     }
 }
 
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
-__device__ __forceinline__ void step_nodes(const StepArgs<typename Store<ST>::R>& a) {
-    using RS = typename Store<ST>::R;
-    using R = std::conditional_t<VW == 2, F2, RS>;
+// One node per thread.  The bound is written as the thread count alone: naming a minimum of one
+// block changes ptxas's register allocation (more registers, fewer resident blocks).
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
     pdl_wait();     // the previous step's stores are complete and visible from here on
     pdl_release();  // every block has started: the next step may be scheduled into freed slots
-    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
-    R f[L::Q];
-    if constexpr (VW == 2)
-        pull2<L, ST>(a, x, y, z, f);
-    else
-        pull<L, ST>(a, x, y, z, f);
-    step_body<L, ST, CLOSURE, FORMULA, FORCE, VW>(a, f, (z * a.ny + y) * a.nx + x);
-}
-
-// One node per thread (the dispatched form).  The bound is written as the thread count alone:
-// naming a minimum of one block changes ptxas's register allocation (more registers, fewer
-// resident blocks).
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, int VW>
-__global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>::R> a) {
-    step_nodes<L, ST, CLOSURE, FORMULA, FORCE, VW>(a);
-}
-
-// Two x-adjacent nodes per thread in packed FP32 pairs, with a minimum number of resident blocks
-// per SM that bounds its registers (3 blocks of 128 threads leave 170 registers a thread, 4 leave
-// 128, 5 leave 102).
-#ifndef LBM_VW2_MIN_BLOCKS
-#define LBM_VW2_MIN_BLOCKS 3
-#endif
-
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128, LBM_VW2_MIN_BLOCKS) k_step_pair(const StepArgs<typename Store<ST>::R> a) {
-    step_nodes<L, ST, CLOSURE, FORMULA, FORCE, 2>(a);
+    typename Store<ST>::R f[L::Q];
+    pull<L, ST>(a, x, y, z, f);
+    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, (z * a.ny + y) * a.nx + x);
 }
 
 // Two x-adjacent nodes per thread that share the pull (paired loads where c_x = 0, adjacent
@@ -1365,9 +1293,9 @@ __global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typenam
     const int node = (z * a.ny + y) * a.nx + x;
     float f[L::Q];
     sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, node);
+    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node);
     sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, node + 1);
+    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -80,15 +80,15 @@ __device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R
                 const int node = (z * a.ny + y) * a.nx + x;
                 R f[L::Q];
                 sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
-                step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, node);
+                step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node);
                 sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
-                step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, node + 1);
+                step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
             }
         } else {
             for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
                 R f[L::Q];
                 pull<L, ST, true>(a, x, y, z, f, es);
-                step_body<L, ST, CLOSURE, FORMULA, FORCE, 1>(a, f, (z * a.ny + y) * a.nx + x, ds);
+                step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, (z * a.ny + y) * a.nx + x, ds);
             }
         }
     }
