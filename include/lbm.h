@@ -51,6 +51,7 @@ extern "C" {
 #define LBM_ERR_NOMEM -3     /* the library's own small allocation failed */
 #define LBM_ERR_NONFINITE -4 /* a global sum came back NaN or infinite */
 #define LBM_ERR_STATE -5     /* call out of order (e.g. lbm_step before lbm_bind) */
+#define LBM_ERR_DRIFT -6     /* the watchdog found the conserved totals off their balance */
 
 /* lattices (the value is q) */
 #define LBM_D2Q9 9
@@ -132,12 +133,13 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
  * NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);
 
-/* Population layout: q arrays of *stride elements of *elem_bytes bytes in each of the two
- * buffers (stride >= N, a multiple of 128).  Any output pointer may be NULL. */
+/* Population layout: the distribution functions f_i(x) of Sec. 2 (eq. (mrteq)) are stored as q
+ * arrays of *stride elements of *elem_bytes bytes in each of the two buffers (stride >= N, a
+ * multiple of 128).  Any output pointer may be NULL. */
 int lbm_layout(const lbm_ctx* ctx, int* q, int64_t* stride, int* elem_bytes);
 
-/* Bind caller-owned device memory and a CUDA stream (cudaStream_t passed as void*, NULL = the
- * legacy default stream).  f_a, f_b: q*stride elements each, 16-byte aligned, distinct.
+/* Bind caller-owned device memory for the populations of eq. (mrteq) and a CUDA stream
+ * (cudaStream_t passed as void*, NULL = the legacy default stream).  f_a, f_b: q*stride elements each, 16-byte aligned, distinct.
  * force_field: d x N values of the compute type when the context was created with
  * p->force_field = 1 (must be non-NULL then), else ignored.  The buffers must stay valid until
  * the context is destroyed or re-bound.  After binding, A is the current buffer. */
@@ -161,8 +163,11 @@ int lbm_bind_tau(lbm_ctx* ctx, void* tau_field);
  * With a closure, s_nu in m_neq is the closure's value at the given gradient. */
 int lbm_init(lbm_ctx* ctx, const double* drho, const double* u, const double* grad_u);
 
-/* Advance n >= 0 time steps: each step pulls f from the current buffer, collides every node
- * with S and tau formed by p->formula, and writes f* to the other buffer, which becomes current.
+/* Advance n >= 0 time steps of the MRT lattice Boltzmann equation, eq. (mrteq) in its moment form
+ * eq. (mrteqvT) (Sec. 2): each step pulls f_i(x) = f*_i(x - c_i) from the current buffer, relaxes
+ * m - m_eq (eq. (meq)) with the diagonal rates of eq. (sD3Q15) at every node, the viscous rates
+ * set by the closure from S of eq. (LuoS) or eq. (ChaiS) (p->formula), adds the discrete force,
+ * and writes f* to the other buffer, which becomes current.
  * n = 0 does nothing.  Asynchronous on the bound stream.  The result does not depend on the
  * schedule (lbm_set_schedule): each node's arithmetic is the same whether the steps are launched
  * one at a time or several per launch.  A multi-step launch orders its tiles through
@@ -201,37 +206,63 @@ int lbm_set_schedule(lbm_ctx* ctx, int schedule);
  * be NULL.  Host-side; no synchronisation. */
 int lbm_stats(const lbm_ctx* ctx, int64_t* steps, int64_t* step_launches);
 
+/* Failure detector: a watchdog on the conservation laws of the scheme.  With every >= 1, each
+ * lbm_step(n) advances in chunks of at most `every` steps and after each chunk computes the
+ * global sums of lbm_sums (synchronising the bound stream) and checks them against reference
+ * sums, taken from the state at the first lbm_step after lbm_set_watchdog, lbm_bind, lbm_init,
+ * lbm_set_state or lbm_adjoint:
+ *  - every sum finite, else LBM_ERR_NONFINITE;
+ *  - the total mass sum delta rho equal to the reference (the collision conserves mass, eq.
+ *    (mrteqvT) with s_0 = 0, and so do the periodic, wall and moving-wall rules), else
+ *    LBM_ERR_DRIFT;
+ *  - on a lattice with every face periodic and no per-node force field, each total momentum
+ *    component equal to the reference plus k N F after k steps (the collision conserves j,
+ *    s_3 = s_5 = s_7 = 0, and the force adds F per node and step), else LBM_ERR_DRIFT.
+ * Each bound is tol * N * rho0 (absolute, in the units of the sums).  On a failure lbm_step
+ * returns at once; the state is the one after the chunk that failed, the steps run so far are
+ * counted by lbm_stats, and lbm_last_error names the quantity, its deviation and the bound.
+ * every = 0 (the default) turns the watchdog off; with it on, lbm_step is synchronous and the
+ * chunking costs one extra read of the populations per chunk (results are unchanged: they do
+ * not depend on how the steps are split into launches).
+ * Errors: LBM_ERR_ARG for every < 0, or a negative or non-finite tol when every > 0. */
+int lbm_set_watchdog(lbm_ctx* ctx, int every, double tol);
+
 /* Synchronise the bound stream and report the library's asynchronous status: LBM_ERR_CUDA for a
  * failed kernel, LBM_ERR_STATE (once; the record is then cleared) when a multi-step launch
  * stopped because a wait for neighbouring units ran out, LBM_OK otherwise (also when nothing is
  * bound). */
 int lbm_status(lbm_ctx* ctx);
 
-/* Strain rate of the state the next step sees, by `formula` (LBM_YU or LBM_CHAI), with the
- * closure solved as in a step.  S_out: ns x N values of the compute type (ns = 6 in 3D, 3 in
+/* Strain rate S_ab = (d_a u_b + d_b u_a)/2 of the state the next step sees (Sec. 3), by
+ * `formula`: LBM_YU, eq. (LuoS) (on D2Q9 and D3Q15 the Yu-type formula of the Sec. 5.4
+ * procedure), or LBM_CHAI, eq. (ChaiS); with the closure solved as in a step.  S_out: ns x N values of the compute type (ns = 6 in 3D, 3 in
  * 2D); tau_out: N values or NULL.  Device pointers.  LBM_YU requires equal viscous rates. */
 int lbm_strain_rate(lbm_ctx* ctx, int formula, void* S_out, void* tau_out);
 
-/* Macroscopic fields of the state the next step sees: drho = sum f (N values) and
- * u = (sum c f + F/2)/rho0 (d x N values), compute type, device pointers (either may be NULL). */
+/* Macroscopic fields of the state the next step sees, as Sec. 2 defines them for the
+ * delta-rho form of eq. (edf): drho = sum f (N values) and u = j/rho0, j = sum c f + F/2 (the
+ * force half-shift of the discrete force) (d x N values), compute type, device pointers (either
+ * may be NULL). */
 int lbm_macroscopic(lbm_ctx* ctx, void* drho_out, void* u_out);
 
-/* Global sums of the state the next step sees, accumulated in FP64 on the device:
- * out[0] = sum delta rho, out[1..d] = sum j (j = sum c f + F/2).  out is a HOST pointer to d+1
+/* Global sums of the state the next step sees, accumulated in FP64 on the device, of the Sec. 2
+ * conserved moments (delta rho and j of eq. (moment)): out[0] = sum delta rho, out[1..d] = sum j
+ * (j = sum c f + F/2).  out is a HOST pointer to d+1
  * doubles.  Synchronises the bound stream.  Returns LBM_ERR_NONFINITE (with out filled) if a sum
  * is NaN or infinite, LBM_ERR_STATE as lbm_status does. */
 int lbm_sums(lbm_ctx* ctx, double* out);
 
-/* Copy the current buffer's populations to dst / from src as a dense q x N array of the storage
- * type (no stride padding).  dst/src may be host or device memory (pinned host memory gives
+/* Copy the current buffer's populations (the state f of eq. (mrteq); checkpoint and restart) to
+ * dst / from src as a dense q x N array of the storage type (no stride padding).  dst/src may be host or device memory (pinned host memory gives
  * asynchronous copies; pageable host memory makes the call synchronous). */
 int lbm_get_state(lbm_ctx* ctx, void* dst);
 int lbm_set_state(lbm_ctx* ctx, const void* src);
 
 /* Allocation-free global sums (the paper has no counterpart: this is a library service).
  *
- * Same result as lbm_sums, for callers that cannot allocate device memory at the point where
- * they need the sums: lbm_create allocates the context's scratch with cudaMalloc, which such
+ * The same sums as lbm_sums, equal to rounding (the rows are split among blocks differently, so
+ * the additions run in another order), for callers that cannot allocate device memory at the
+ * point where they need the sums: lbm_create allocates the context's scratch with cudaMalloc, which such
  * callers must avoid, e.g. code whose device memory belongs to another allocator (a framework's
  * caching pool) or a time-stepping loop with a latency budget (cudaMalloc / cudaFree may
  * synchronise the device and take unbounded time).  No context is used and nothing is allocated:
@@ -247,10 +278,13 @@ int lbm_set_state(lbm_ctx* ctx, const void* src);
  *  stream   cudaStream_t as void* (NULL = legacy default stream); the call synchronises it.
  * The scratch is one static device array of LBM_NOALLOC_MAX_BLOCKS x 4 partial sums (plus 4
  * doubles) that every GPU loading the library holds until the process exits.  Lattices with
- * more than LBM_NOALLOC_MAX_ROWS rows (ny * nz) are rejected with LBM_ERR_ARG, as are the other
- * argument errors of lbm_create; a rejected call touches no CUDA state.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Each call writes every scratch slot it reads,
+ * more than LBM_NOALLOC_MAX_ROWS rows (ny * nz) are rejected with LBM_ERR_ARG, as are the
+ * argument errors of lbm_create that apply here (dimensions, precision, rho0 > 0 and finite,
+ * finite force and wall velocities, boundary pairs); a rejected call touches no CUDA state.
+ * Every call looks up the array's device address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing), so the call stays valid after a device reset.  The call synchronises
+ * its stream, so it must not be called while that stream is being captured into a CUDA graph.
+ * Each call writes every scratch slot it reads,
  * so nothing has to be cleared between calls, but all calls share the one array: calls whose
  * kernels can overlap on the GPU (other streams or host threads) race and must be serialised.
  * Returns LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, or LBM_ERR_NONFINITE (out filled) for a NaN or

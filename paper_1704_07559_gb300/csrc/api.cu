@@ -39,6 +39,13 @@ struct lbm_ctx {
     int stream_rows, stream_tiles;
     int schedule;
     long long n_steps, n_step_launches;  // steps advanced and step kernels launched by lbm_step
+    // watchdog (lbm_set_watchdog): check the global sums every watch_every steps against the
+    // reference sums watch_ref taken at step watch_ref_step (watch_ref_ok 0: take it first)
+    int watch_every;
+    double watch_tol;
+    int watch_ref_ok;
+    double watch_ref[4];
+    long long watch_ref_step;
     char err[512];
 };
 
@@ -301,6 +308,98 @@ int check_bound(lbm_ctx* c) {
     return LBM_OK;
 }
 
+
+// Global sums of the current state into out[0..d] (HOST), synchronising the bound stream:
+// LBM_ERR_CUDA, LBM_ERR_STATE (a multi-step launch's wait ran out), LBM_ERR_NONFINITE (out
+// filled) or LBM_OK.
+int sums_now(lbm_ctx* c, double* out, const char* who) {
+    cudaError_t e;
+    const Tag t = tag_of(c->q, c->p.precision);
+    if (c->p.precision == LBM_FP64) {
+        lbm::StepArgs<double> a;
+        fill_args(c, &a);
+        set_buffers(c, &a, c->buf[c->cur], nullptr);
+        switch (t) {
+            case T_D3Q19_F64: e = lbm::sums_d3q19_f64(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_F64: e = lbm::sums_d3q15_f64(a, c->partial, c->result, c->stream); break;
+            case T_D2Q9_F64: e = lbm::sums_d2q9_f64(a, c->partial, c->result, c->stream); break;
+            default: e = cudaErrorInvalidValue;
+        }
+    } else {
+        lbm::StepArgs<float> a;
+        fill_args(c, &a);
+        set_buffers(c, &a, c->buf[c->cur], nullptr);
+        switch (t) {
+            case T_D3Q19_F32: e = lbm::sums_d3q19_f32(a, c->partial, c->result, c->stream); break;
+            case T_D3Q19_F16: e = lbm::sums_d3q19_f16(a, c->partial, c->result, c->stream); break;
+            case T_D3Q19_BF16: e = lbm::sums_d3q19_bf16(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_F32: e = lbm::sums_d3q15_f32(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_F16: e = lbm::sums_d3q15_f16(a, c->partial, c->result, c->stream); break;
+            case T_D3Q15_BF16: e = lbm::sums_d3q15_bf16(a, c->partial, c->result, c->stream); break;
+            case T_D2Q9_F32: e = lbm::sums_d2q9_f32(a, c->partial, c->result, c->stream); break;
+            default: e = cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    e = cudaMemcpyAsync(out, c->result, sizeof(double) * (1 + c->d), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    int rc = stream_flag(c);
+    if (rc) return rc;
+    for (int k = 0; k <= c->d; ++k)
+        if (!is_finite(out[k])) return fail(c, LBM_ERR_NONFINITE, "%s: non-finite sum %d (%g)", who, k, out[k]);
+    return LBM_OK;
+}
+
+// The watchdog's test of sums s taken after step c->n_steps: the total mass stays at the
+// reference, and on an all-periodic lattice without a force field each momentum component grows
+// by N F per step from the reference (halfway bounce-back walls exchange momentum with the
+// fluid, and a per-node force field's total is not known to the library); bound tol * N * rho0.
+int watch_check(lbm_ctx* c, const double* s) {
+    const double bound = c->watch_tol * (double)c->N * c->p.rho0;
+    const long long k = c->n_steps - c->watch_ref_step;
+    const double dm = s[0] - c->watch_ref[0];
+    if (!(std::fabs(dm) <= bound))
+        return fail(c, LBM_ERR_DRIFT, "watchdog: total mass changed by %.6g over %lld steps (bound %.6g)", dm, k, bound);
+    bool periodic = true;
+    for (int f = 0; f < 2 * c->d; ++f) periodic = periodic && c->p.bc[f] == LBM_PERIODIC;
+    if (periodic && !c->p.force_field) {
+        for (int a = 0; a < c->d; ++a) {
+            const double dj = s[1 + a] - (c->watch_ref[1 + a] + (double)k * (double)c->N * c->force[a]);
+            if (!(std::fabs(dj) <= bound))
+                return fail(c, LBM_ERR_DRIFT,
+                            "watchdog: total momentum %d is %.6g away from its balance over %lld steps (bound %.6g)", a,
+                            dj, k, bound);
+        }
+    }
+    return LBM_OK;
+}
+
+// lbm_step(n) under the watchdog: chunks of at most watch_every steps, the sums checked after each
+int step_watched(lbm_ctx* c, int n) {
+    if (!c->watch_ref_ok) {
+        int rc = sums_now(c, c->watch_ref, "watchdog reference");
+        if (rc) return rc;
+        c->watch_ref_ok = 1;
+        c->watch_ref_step = c->n_steps;
+    }
+    for (int done = 0; done < n;) {
+        const int k = std::min(c->watch_every, n - done);
+        long long launches = 0;
+        cudaError_t e = advance(c, k, &launches);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
+        c->n_steps += k;
+        c->n_step_launches += launches;
+        done += k;
+        double s[4];
+        int rc = sums_now(c, s, "watchdog");
+        if (rc) return rc;
+        rc = watch_check(c, s);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
 
 // ------------------------------------------------------------------------------------------
 // adjoint driver helpers
@@ -662,6 +761,16 @@ int lbm_set_schedule(lbm_ctx* c, int schedule) {
     return LBM_OK;
 }
 
+int lbm_set_watchdog(lbm_ctx* c, int every, double tol) {
+    if (!c) return LBM_ERR_ARG;
+    if (every < 0) return fail(c, LBM_ERR_ARG, "lbm_set_watchdog: every < 0");
+    if (every > 0 && !(tol >= 0.0 && is_finite(tol))) return fail(c, LBM_ERR_ARG, "lbm_set_watchdog: tol");
+    c->watch_every = every;
+    c->watch_tol = tol;
+    c->watch_ref_ok = 0;
+    return LBM_OK;
+}
+
 int lbm_status(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
     if (!c->bound) return LBM_OK;
@@ -689,6 +798,7 @@ int lbm_bind(lbm_ctx* c, void* f_a, void* f_b, const void* force_field, void* st
     c->stream = static_cast<cudaStream_t>(stream);
     c->bound = 1;
     c->cur = 0;
+    c->watch_ref_ok = 0;
     c->err[0] = '\0';
     return LBM_OK;
 }
@@ -757,6 +867,7 @@ int lbm_init(lbm_ctx* c, const double* drho, const double* u, const double* grad
         default: return fail(c, LBM_ERR_ARG, "lbm_init: unsupported lattice/precision");
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_init");
+    c->watch_ref_ok = 0;
     return LBM_OK;
 }
 
@@ -764,6 +875,7 @@ int lbm_step(lbm_ctx* c, int n) {
     int rc = check_bound(c);
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_ERR_ARG, "lbm_step: n < 0");
+    if (c->watch_every > 0 && n > 0) return step_watched(c, n);
     long long launches = 0;
     cudaError_t e = advance(c, n, &launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
@@ -797,43 +909,7 @@ int lbm_sums(lbm_ctx* c, double* out) {
     int rc = check_bound(c);
     if (rc) return rc;
     if (!out) return fail(c, LBM_ERR_ARG, "lbm_sums: out is required");
-    cudaError_t e;
-    const Tag t = tag_of(c->q, c->p.precision);
-    if (c->p.precision == LBM_FP64) {
-        lbm::StepArgs<double> a;
-        fill_args(c, &a);
-        set_buffers(c, &a, c->buf[c->cur], nullptr);
-        switch (t) {
-            case T_D3Q19_F64: e = lbm::sums_d3q19_f64(a, c->partial, c->result, c->stream); break;
-            case T_D3Q15_F64: e = lbm::sums_d3q15_f64(a, c->partial, c->result, c->stream); break;
-            case T_D2Q9_F64: e = lbm::sums_d2q9_f64(a, c->partial, c->result, c->stream); break;
-            default: e = cudaErrorInvalidValue;
-        }
-    } else {
-        lbm::StepArgs<float> a;
-        fill_args(c, &a);
-        set_buffers(c, &a, c->buf[c->cur], nullptr);
-        switch (t) {
-            case T_D3Q19_F32: e = lbm::sums_d3q19_f32(a, c->partial, c->result, c->stream); break;
-            case T_D3Q19_F16: e = lbm::sums_d3q19_f16(a, c->partial, c->result, c->stream); break;
-            case T_D3Q19_BF16: e = lbm::sums_d3q19_bf16(a, c->partial, c->result, c->stream); break;
-            case T_D3Q15_F32: e = lbm::sums_d3q15_f32(a, c->partial, c->result, c->stream); break;
-            case T_D3Q15_F16: e = lbm::sums_d3q15_f16(a, c->partial, c->result, c->stream); break;
-            case T_D3Q15_BF16: e = lbm::sums_d3q15_bf16(a, c->partial, c->result, c->stream); break;
-            case T_D2Q9_F32: e = lbm::sums_d2q9_f32(a, c->partial, c->result, c->stream); break;
-            default: e = cudaErrorInvalidValue;
-        }
-    }
-    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums");
-    e = cudaMemcpyAsync(out, c->result, sizeof(double) * (1 + c->d), cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums copy");
-    e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sums sync");
-    rc = stream_flag(c);
-    if (rc) return rc;
-    for (int k = 0; k <= c->d; ++k)
-        if (!is_finite(out[k])) return fail(c, LBM_ERR_NONFINITE, "lbm_sums: non-finite sum %d", k);
-    return LBM_OK;
+    return sums_now(c, out, "lbm_sums");
 }
 
 int lbm_get_state(lbm_ctx* c, void* dst) {
@@ -857,6 +933,7 @@ int lbm_set_state(lbm_ctx* c, const void* src) {
                         ? cudaMemcpyAsync(c->buf[c->cur], src, row * c->q, cudaMemcpyDefault, c->stream)
                         : cudaMemcpy2DAsync(c->buf[c->cur], pitch, src, row, row, c->q, cudaMemcpyDefault, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_state");
+    c->watch_ref_ok = 0;
     return LBM_OK;
 }
 
@@ -885,6 +962,7 @@ int lbm_adjoint(lbm_ctx* c, int T, int seg, void* work, int64_t work_bytes, doub
                         ? adjoint_run<double>(c, T, seg, static_cast<char*>(work), L, dLdg, loss)
                         : adjoint_run<float>(c, T, seg, static_cast<char*>(work), L, dLdg, loss);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint");
+    c->watch_ref_ok = 0;  // the current state is now the one after T steps
     if (!is_finite(*loss)) return fail(c, LBM_ERR_NONFINITE, "lbm_adjoint: non-finite functional");
     return LBM_OK;
 }

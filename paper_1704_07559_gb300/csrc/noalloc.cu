@@ -14,7 +14,7 @@
 // (different streams, or different host threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <cmath>
 
 #include "../../include/lbm.h"
 #include "launch.h"
@@ -25,28 +25,19 @@ namespace {
 constexpr int ROWS_PER_BLOCK = LBM_NOALLOC_MAX_ROWS / LBM_NOALLOC_MAX_BLOCKS;
 constexpr int MAX_BLOCKS = LBM_NOALLOC_MAX_BLOCKS;
 constexpr int WIDTH = 4;  // 1 + d for the widest lattice
-constexpr int MAX_DEVICES = 64;
 
 // the scratch: partial rows, then the final row of sums
 static __device__ __align__(256) double g_noalloc_scratch[MAX_BLOCKS * WIDTH + WIDTH];
 
-std::mutex g_lock;
-double* g_ptr[MAX_DEVICES] = {};
-
-// Device address of the static scratch for the current device, looked up once per device.
+// Device address of the static scratch on the current device.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up, on every call: the lookup allocates
+// nothing and costs little, and an address kept from an earlier call could be stale after a
+// device reset (the module, and with it the array, is loaded again in the new context).
 cudaError_t scratch_for_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_ptr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 
@@ -94,7 +85,12 @@ extern "C" int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_p
     if (nx < 1 || ny < 1 || nz < 1 || (d == 2 && nz != 1) || ny > 65535 || nz > 65535) return LBM_ERR_ARG;
     const long long N = (long long)nx * ny * nz;
     if (N >= (1LL << 31) || stride < N) return LBM_ERR_ARG;
-    if (!(p->rho0 > 0.0)) return LBM_ERR_ARG;
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return LBM_ERR_ARG;
+    for (int a = 0; a < d; ++a)
+        if (force && !std::isfinite(force[a])) return LBM_ERR_ARG;
+    for (int fc = 0; fc < 2 * d; ++fc)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(p->lid_u[fc][k])) return LBM_ERR_ARG;
     for (int a = 0; a < d; ++a) {
         const int f0 = p->bc[2 * a], f1 = p->bc[2 * a + 1];
         if (f0 < LBM_PERIODIC || f0 > LBM_LID || f1 < LBM_PERIODIC || f1 > LBM_LID) return LBM_ERR_ARG;

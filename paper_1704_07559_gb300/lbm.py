@@ -24,11 +24,12 @@ FORMULA = {"yu": 0, "chai": 1}
 BC = {"periodic": 0, "wall": 1, "lid": 2}
 SCHEDULE = {"auto": 0, "per_step": 1, "stream": 2, "stall_check": 3}
 STORAGE_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}
-ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_STATE"}
+ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_STATE",
+          -6: "LBM_ERR_DRIFT"}
 API = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_layout", "lbm_bind", "lbm_bind_tau", "lbm_init",
        "lbm_step", "lbm_strain_rate", "lbm_macroscopic", "lbm_sums", "lbm_get_state", "lbm_set_state", "lbm_last_error",
        "lbm_sums_noalloc", "lbm_adjoint_workspace", "lbm_adjoint", "lbm_set_schedule", "lbm_status",
-       "lbm_stats"]
+       "lbm_stats", "lbm_set_watchdog"]
 
 
 class LBMError(RuntimeError):
@@ -83,6 +84,7 @@ def lib():
     L.lbm_step.argtypes = [vp, ctypes.c_int]
     L.lbm_set_schedule.argtypes = [vp, ctypes.c_int]
     L.lbm_status.argtypes = [vp]
+    L.lbm_set_watchdog.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.lbm_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_int, vp, vp]
     L.lbm_macroscopic.argtypes = [vp, vp, vp]
@@ -221,6 +223,12 @@ class Lattice:
     def set_schedule(self, schedule):
         """How step(n >= 2) launches: "auto", "per_step" or "stream" (several steps per launch)."""
         self._check(lib().lbm_set_schedule(self.ctx, SCHEDULE[schedule]))
+        return self
+
+    def set_watchdog(self, every, tol=1e-6):
+        """Check the conserved totals every `every` steps inside step() (0 turns it off); step()
+        then raises LBMError LBM_ERR_DRIFT or LBM_ERR_NONFINITE when they go off balance."""
+        self._check(lib().lbm_set_watchdog(self.ctx, int(every), float(tol)))
         return self
 
     def stats(self):

@@ -116,6 +116,47 @@ def test_null_context_calls_fail_cleanly(L):
     assert L.lbm_set_schedule(None, 0) == -1
     assert L.lbm_status(None) == -1
     assert L.lbm_stats(None, None, None) == -1
+    assert L.lbm_set_watchdog(None, 1, 1e-6) == -1
+
+
+def test_noalloc_rejects_bad_arguments_before_any_cuda_call(L):
+    """lbm_sums_noalloc checks its arguments on the host first (a rejected call touches no CUDA
+    state, so these run without a GPU): a non-finite or non-positive rho0, a non-finite force or
+    wall velocity, an unpaired boundary, a row count beyond its static scratch."""
+    from paper_1704_07559_gb300 import lbm
+
+    fn = L.lbm_sums_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lbm.Params),
+                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    out = (ctypes.c_double * 4)()
+
+    def call(mutate=None, force=None, dims=(4, 4, 4)):
+        p = lbm.default_params()
+        if mutate:
+            mutate(p)
+        fv = None if force is None else (ctypes.c_double * 3)(*force)
+        n = dims[0] * dims[1] * dims[2]
+        return fn(19, dims[0], dims[1], dims[2], ctypes.byref(p), fv, ctypes.c_void_p(256), n, None, out, None)
+
+    inf, nan = float("inf"), float("nan")
+    assert call(lambda p: setattr(p, "rho0", inf)) == -1
+    assert call(lambda p: setattr(p, "rho0", 0.0)) == -1
+    assert call(lambda p: setattr(p, "rho0", nan)) == -1
+    assert call(force=(1e-6, nan, 0.0)) == -1
+    assert call(force=(inf, 0.0, 0.0)) == -1
+
+    def lid_nan(p):
+        p.bc[2], p.bc[3] = 1, 2
+        p.lid_u[3][0] = nan
+    assert call(lid_nan) == -1
+
+    def unpaired(p):
+        p.bc[2] = 1
+    assert call(unpaired) == -1
+    assert call(dims=(4, 1024, 257)) == -1
+    assert call(lambda p: setattr(p, "precision", 7)) == -1
 
 
 def header_constants(prefix):

@@ -60,12 +60,16 @@ CASES = [
     dict(q=15, dims=(50, 12, 7), precision="fp32", bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
          force=[1e-5, 0.0, 2e-6], tol=1e-6),
     dict(q=15, dims=(40, 10, 6), precision="bf16s", bc=None, force=[2e-6, 0.0, 0.0], tol=1e-6),
+    dict(q=19, dims=(48, 10, 7), precision="fp16s", bc=["periodic"] * 2 + ["wall"] * 2 + ["periodic"] * 2,
+         force=[1e-5, 0.0, 0.0], tol=1e-6),
+    dict(q=19, dims=(33, 9, 6), precision="fp32", bc=None, force=None, force_field=True, tol=1e-6),
 ]
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", CASES, ids=["d3q19-fp32-channel", "d3q19-fp64-periodic", "d2q9-fp32-lid",
-                                           "d3q15-fp32-channel", "d3q15-bf16-periodic"])
+                                           "d3q15-fp32-channel", "d3q15-bf16-periodic", "d3q19-fp16-channel",
+                                           "d3q19-fp32-force-field"])
 def test_matches_lbm_sums_on_two_calls_in_a_row(case):
     """Two calls in a row (before and after a step, so the scratch holds the first call's
     contents when the second runs) agree with lbm_sums within the sums tolerance of the parity
@@ -75,8 +79,13 @@ def test_matches_lbm_sums_on_two_calls_in_a_row(case):
     fn = entry()
     q = case["q"]
     rng = np.random.default_rng(11)
+    ff = None
+    if case.get("force_field"):
+        d = 2 if q == 9 else 3
+        ff = torch.tensor(rng.normal(scale=1e-5, size=(d,) + tuple(reversed(case["dims"]))), dtype=torch.float32)
     lat = lbm.Lattice(q, *case["dims"], rates={19: RATES19, 15: RATES15, 9: RATES9}[q], precision=case["precision"],
-                      closure="smag", smag_cs=0.17, bc=case["bc"], lid_u=case.get("lid"), force=case["force"])
+                      closure="smag", smag_cs=0.17, bc=case["bc"], lid_u=case.get("lid"), force=case["force"],
+                      force_field=ff)
     d = lat.d
     lat.init(rng.normal(scale=1e-3, size=lat.shape), rng.normal(scale=0.02, size=(d,) + lat.shape),
              rng.normal(scale=2e-3, size=(d * d,) + lat.shape))
@@ -89,3 +98,30 @@ def test_matches_lbm_sums_on_two_calls_in_a_row(case):
         fmax = float(cur[:, :lat.N].abs().max().to(torch.float64))
         assert np.abs(got - ref).max() <= case["tol"] * lat.N * fmax, (call_no, got, ref)
         lat.step(1)
+
+
+@pytest.mark.gpu
+def test_allocates_nothing():
+    """The property the entry point exists for: after one warm-up call (which loads the module
+    and with it the static array), repeated calls leave the device's free memory unchanged; and
+    torch's caching allocator sees no allocation either."""
+    import torch
+
+    fn = entry()
+    lat = lbm.Lattice(19, 64, 24, 16, rates=RATES19, precision="fp32", closure="smag", smag_cs=0.17,
+                      force=[1e-5, 0.0, 0.0])
+    rng = np.random.default_rng(5)
+    lat.init(rng.normal(scale=1e-3, size=lat.shape), rng.normal(scale=0.02, size=(3,) + lat.shape))
+    rc, first = call(fn, lat, lat.f_a, [1e-5, 0.0, 0.0])
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(20):
+        rc, got = call(fn, lat, lat.f_a, [1e-5, 0.0, 0.0])
+        assert rc == 0
+        assert np.array_equal(got, first)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
