@@ -1,8 +1,11 @@
 """Parity at the full workload sizes, through the same library calls and launches that bench.py
 times (its own workload constructors build every lattice here).
 
-After a few GPU steps, the strain-rate read-outs and the next step are compared with the FP64
-oracle at sampled nodes: corners, face and edge centres, and seeded random nodes.  For each
+The headline channel (256 x 128 x 128) is compared whole: every node's read-outs and populations
+against the oracle run over z-slabs in parallel host processes.  The other workloads (the 512^3
+box, the 4096^2 cavity) and the channel's variants are compared at sampled nodes: after a few GPU
+steps, the strain-rate read-outs and the next step are compared with the FP64 oracle at sampled
+nodes: corners, face and edge centres, and seeded random nodes.  For each
 sampled node the oracle gets the node's neighbourhood, a patch of up to 3 x 3 x 3 nodes cut from
 the GPU's populations (converted exactly to float64) with the workload's boundary kind on every
 face the node touches, and computes that node's collision on its own (or_node).  Bars are those
@@ -151,6 +154,45 @@ def test_channel_256x128x128_sampled(lattice, precision, formula, closure):
                       smag_cs=bench.CS)
     assert np.abs(S).max() > 1e-4  # the sample carries a real strain rate
     lat.close()
+
+
+@pytest.mark.parametrize("precision,formula", [("fp32", "yu"), ("fp32", "chai"), ("fp16s", "yu")])
+def test_channel_256x128x128_whole_array(precision, formula):
+    """The headline channel compared with the oracle at every one of its 4.2M nodes, through the
+    headline's own launch.  After 20 steps (the automatic schedule: one multi-step launch), the
+    read-outs of that state by both formulas (eqs. (LuoS), (ChaiS)) and tau are compared whole;
+    then two more steps run as one multi-step launch and the populations after them are compared
+    whole with two oracle steps from the same state.  The oracle runs over z-slabs in one spawned
+    process per host core (oracle/slabs.py, bit-identical to the whole-grid oracle).  Bars: S and
+    tau 1e-5 (normwise); populations after two steps 2 x the one-step FP32 bound (2e-6 max|f|) per
+    element, and for 16-bit storage 2 x one unit roundoff of the format of max|f| on top (two
+    roundings, each carried by one step)."""
+    from oracle import slabs
+
+    t = TOL[precision]
+    lat = bench.make_lattice(precision, formula)
+    lat.step(20)
+    steps0, launches0 = lat.stats()
+    f20 = lat.get_state().to(torch.float64).cpu().numpy()
+    reads = {fm: [x.to(torch.float64).cpu().numpy() for x in lat.strain_rate(fm, with_tau=True)]
+             for fm in ("yu", "chai")}
+    lat.step(2)
+    steps1, launches1 = lat.stats()
+    assert (steps1 - steps0, launches1 - launches0) == (2, 1)  # one multi-step launch
+    f22 = lat.get_state().to(torch.float64).cpu().numpy()
+    lat.close()
+    kw = dict(q=19, rates=bench.RATES, closure=O.SMAG, smag_cs=bench.CS, formula=O.YU if formula == "yu" else O.CHAI,
+              bc=[BCN[b] for b in bench.BC], pl_tol=1e-7)
+    fo, ro = slabs.run(kw, f20, steps=2, force=np.array([bench.G, 0.0, 0.0]), readouts=("yu", "chai"))
+    for fm in ("yu", "chai"):
+        S, tau = reads[fm]
+        assert relerr(S, ro[fm][0]) <= t["S"], (fm, relerr(S, ro[fm][0]))
+        assert relerr(tau, ro[fm][1]) <= t["S"], (fm, relerr(tau, ro[fm][1]))
+    assert np.abs(reads["yu"][0]).max() > 1e-4  # the state carries a real strain rate
+    fmax = np.abs(fo).max()
+    bound = 2 * t["f"] * fmax + 2 * t.get("eps", 0.0) * fmax
+    err = np.abs(f22 - fo)
+    assert np.all(err <= bound), (err.max() / fmax, bound / fmax)
 
 
 @pytest.mark.parametrize("precision,formula", [("fp32", "yu"), ("fp16s", "chai"), ("bf16s", "yu")])
