@@ -723,41 +723,85 @@ struct Eq<D2Q9> {
     static constexpr double YU_A = 1.0 / 4.0;
 };
 
-// He-Luo equilibrium (eq. (edf), delta-rho form) and the discrete force in opposite-pair form:
-// Pe_p = feq_a + feq_b = 2 w (drho + 4.5 (c.j)(c.u) - 1.5 j.u), De_p = feq_a - feq_b = 6 w c.j;
-// PF_p = Fbar_a + Fbar_b = 2 w (9 (c.u)(c.F) - 3 u.F), DF_p = 6 w c.F;
-// rest: fe0 = w0 (drho - 1.5 j.u), F0 = -3 w0 u.F.  (c = c_a, w = w_a, u = j / rho0.)
+// Chai route: the effective non-equilibrium distributions f - f_eq + Fbar/2 of the He-Luo
+// equilibrium (eq. (edf)) and the Guo-type force, in opposite-pair form, formed directly.  With
+// cj = c.j, cu = c.u, cF = c.F (c = c_a of pair p, weight w), g = u.(j - F) and
+// B = 2 drho - 3 g, f_eq_a + f_eq_b = 2w (drho + 4.5 cj cu - 1.5 j.u), f_eq_a - f_eq_b = 6 w cj,
+// Fbar_a + Fbar_b = 2w (9 cu cF - 3 u.F), Fbar_a - Fbar_b = 6 w cF, Fbar_0 = -3 w0 u.F, so that
+//   (f_eq - Fbar/2)_a + (f_eq - Fbar/2)_b = w B + 9 w cu (cj - cF),
+//   (f_eq - Fbar/2)_a - (f_eq - Fbar/2)_b = 3 w (2 cj - cF),
+//   (f_eq - Fbar/2)_0 = w0 B / 2.
+// Pn_p = P_p - (first), Dn_p = D_p - (second), fn0 = f0 - (third).
 template <class L, bool FORCE, class R>
-__device__ __forceinline__ void equilibrium_pairs(R drho, const R (&j)[3], const R (&u)[3], const R (&F)[3], R& fe0,
-                                                  R (&Pe)[L::NP], R (&De)[L::NP], R& F0, R (&PF)[L::NP],
-                                                  R (&DF)[L::NP]) {
-    const R ju = fma(j[0], u[0], fma(j[1], u[1], j[2] * u[2]));
-    const R base = fma(R(-1.5f), ju, drho);
+__device__ __forceinline__ void noneq_pairs(R f0, const R (&P)[L::NP], const R (&Dd)[L::NP], R drho, const R (&j)[3],
+                                            const R (&u)[3], const R (&F)[3], R& fn0, R (&Pn)[L::NP],
+                                            R (&Dn)[L::NP]) {
+    R g = fma(j[0], u[0], fma(j[1], u[1], j[2] * u[2]));
+    if constexpr (FORCE) g = fma(-u[0], F[0], fma(-u[1], F[1], fma(-u[2], F[2], g)));
+    const R B = fma(R(-3.0f), g, R(2.0f) * drho);
     constexpr double w0 = double(L::wnum(0)) / L::WDEN;
-    fe0 = cst<R>(w0) * base;
-    R uF = R(0.0f);
-    if constexpr (FORCE) {
-        uF = fma(u[0], F[0], fma(u[1], F[1], u[2] * F[2]));
-        F0 = cst<R>(-3.0 * w0) * uF;
-    } else {
-        F0 = R(0.0f);
-    }
+    fn0 = fma(cst<R>(-0.5 * w0), B, f0);
     sfor<L::NP>([&](auto p) {
         constexpr int i = L::pa(CV(p));
         constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
         constexpr double w = double(L::wnum(i)) / L::WDEN;
         const R cj = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), j[0]), j[1]), j[2]);
         const R cu = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), u[0]), u[1]), u[2]);
-        Pe[p] = cst<R>(2.0 * w) * fma(R(4.5f) * cj, cu, base);
-        De[p] = cst<R>(6.0 * w) * cj;
+        R t = cj, t2 = R(2.0f) * cj;
         if constexpr (FORCE) {
             const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
-            PF[p] = cst<R>(2.0 * w) * fma(R(9.0f) * cu, cF, R(-3.0f) * uF);
-            DF[p] = cst<R>(6.0 * w) * cF;
-        } else {
-            PF[p] = R(0.0f);
-            DF[p] = R(0.0f);
+            t = cj - cF;
+            t2 = fma(R(2.0f), cj, -cF);
         }
+        Pn[p] = fma(cst<R>(-9.0 * w) * cu, t, fma(cst<R>(-w), B, P[p]));
+        Dn[p] = fma(cst<R>(-3.0 * w), t2, Dd[p]);
+    });
+}
+
+// f <- f - Omega_f + Fbar for the Chai route, Omega_f given by its opposite-pair even / odd parts
+// (Ef0 for the rest population), Fbar the Guo-type discrete force in the pair form above.
+template <class L, bool FORCE, class R>
+__device__ __forceinline__ void fold_fixed_part(R (&f)[L::Q], R Ef0, const R (&Ef)[L::NP], const R (&Of)[L::NP],
+                                                const R (&u)[3], const R (&F)[3]) {
+    constexpr double w0 = double(L::wnum(0)) / L::WDEN;
+    R uF = R(0.0f);
+    if constexpr (FORCE) {
+        uF = fma(u[0], F[0], fma(u[1], F[1], u[2] * F[2]));
+        f[0] = fma(cst<R>(-3.0 * w0), uF, f[0] - Ef0);
+    } else {
+        f[0] -= Ef0;
+    }
+    sfor<L::NP>([&](auto p) {
+        constexpr int i = L::pa(CV(p));
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        constexpr double w = double(L::wnum(i)) / L::WDEN;
+        R e = Ef[p], o = Of[p];
+        if constexpr (FORCE) {
+            const R cu = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), u[0]), u[1]), u[2]);
+            const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
+            e -= fma(cst<R>(9.0 * w) * cu, cF, cst<R>(-3.0 * w) * uF);  // Fbar even part / 2
+            o = fma(cst<R>(-3.0 * w), cF, o);                            // Fbar odd part / 2
+        }
+        f[L::pa(CV(p))] -= e + o;
+        f[L::pb(CV(p))] -= e - o;
+    });
+}
+
+// The Guo-type discrete force Fbar_i (pair form above), population by population.
+template <class L, class R>
+__device__ __forceinline__ void force_bar(const R (&u)[3], const R (&F)[3], R (&Fb)[L::Q]) {
+    constexpr double w0 = double(L::wnum(0)) / L::WDEN;
+    const R uF = fma(u[0], F[0], fma(u[1], F[1], u[2] * F[2]));
+    Fb[0] = cst<R>(-3.0 * w0) * uF;
+    sfor<L::NP>([&](auto p) {
+        constexpr int i = L::pa(CV(p));
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        constexpr double w = double(L::wnum(i)) / L::WDEN;
+        const R cu = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), u[0]), u[1]), u[2]);
+        const R cF = cadd<cz>(cadd<cy>(cadd<cx>(nzero<R>(), F[0]), F[1]), F[2]);
+        const R e = fma(cst<R>(9.0 * w) * cu, cF, cst<R>(-3.0 * w) * uF), o = cst<R>(3.0 * w) * cF;
+        Fb[L::pa(CV(p))] = e + o;
+        Fb[L::pb(CV(p))] = e - o;
     });
 }
 
@@ -1151,19 +1195,8 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
             j[d] = FORCE ? fma(R(0.5f), F[d], acc) : acc;
             u[d] = j[d] * ir0;
         });
-        R fe0, Pe[NP], De[NP], F0, PF[NP], DF[NP];
-        equilibrium_pairs<L, FORCE>(drho, j, u, F, fe0, Pe, De, F0, PF, DF);
-        R fn0 = f[0] - fe0, Pn[NP], Dn[NP];
-        if constexpr (FORCE) fn0 = fma(R(0.5f), F0, fn0);
-        sfor<NP>([&](auto p) {
-            if constexpr (FORCE) {
-                Pn[p] = fma(R(0.5f), PF[p], P[p] - Pe[p]);
-                Dn[p] = fma(R(0.5f), DF[p], Dd[p] - De[p]);
-            } else {
-                Pn[p] = P[p] - Pe[p];
-                Dn[p] = Dd[p] - De[p];
-            }
-        });
+        R fn0, Pn[NP], Dn[NP];
+        noneq_pairs<L, FORCE>(f[0], P, Dd, drho, j, u, F, fn0, Pn, Dn);
         R mn[Q];
         Xf<L>::forward(fn0, Pn, Dn, mn);
         const R kS = R(-1.5f) * ir0;  // S = -N / (2 rho0 cs2)
@@ -1185,6 +1218,11 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
             snu = R(a.s[L::NU0]);
             if (a.readout) goto readout;
             sfor<Q>([&](auto i) { out[i] = Om[i]; });
+            if constexpr (FORCE) {  // f* = f - Omega + Fbar
+                R Fb[Q];
+                force_bar<L>(u, F, Fb);
+                sfor<Q>([&](auto i) { out[i] -= Fb[i]; });
+            }
         } else {
             R Df[Q], Dv[Q];
             sfor<Q>([&](auto k) {
@@ -1214,17 +1252,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
             }
             // f* = f - Omega_f + Fbar - s_nu Omega_v: everything but the last term is folded into f
             // now, so only f and Omega_v stay live across the closure
-            f[0] -= Ef0;
-            if constexpr (FORCE) f[0] += F0;
-            sfor<NP>([&](auto p) {
-                R da = Ef[p] + Of[p], db = Ef[p] - Of[p];
-                if constexpr (FORCE) {
-                    da = fma(R(-0.5f), PF[p] + DF[p], da);
-                    db = fma(R(-0.5f), PF[p] - DF[p], db);
-                }
-                f[L::pa(CV(p))] -= da;
-                f[L::pb(CV(p))] -= db;
-            });
+            fold_fixed_part<L, FORCE>(f, Ef0, Ef, Of, u, F);
             tau = solve_tau<L, R, CLOSURE>(A, B, a, S, snu, node, tau_prev);
             if (a.readout) goto readout;
             out[0] = snu * Ev0;
@@ -1232,13 +1260,6 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
                 const R e = snu * Ev[p];
                 out[L::pa(CV(p))] = e;
                 out[L::pb(CV(p))] = e;
-            });
-        }
-        if constexpr (FORCE && CLOSURE == CL_NEWTON) {  // f* = f - Omega + Fbar
-            out[0] -= F0;
-            sfor<NP>([&](auto p) {
-                out[L::pa(CV(p))] = fma(R(-0.5f), PF[p] + DF[p], out[L::pa(CV(p))]);
-                out[L::pb(CV(p))] = fma(R(-0.5f), PF[p] - DF[p], out[L::pb(CV(p))]);
             });
         }
     }
