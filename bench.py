@@ -214,17 +214,6 @@ def _oracle_channel_box(nx, ny, nz):
     return Gr, Gr.init(drho, u, force=F), F
 
 
-def _oracle_replica(job):
-    """One host process: `steps` oracle steps on its own copy of a channel sub-box; returns
-    (node updates, seconds)."""
-    (nx, ny, nz), steps = job
-    Gr, f, F = _oracle_channel_box(nx, ny, nz)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        f, _ = Gr.step(f, force=F)
-    return Gr.N * steps, time.perf_counter() - t0
-
-
 def job_rate(ms_local, updates_local, dist=None, device="cpu"):
     """Whole-job rate of N replicas: the slowest rank's time of the timed region (max over ranks)
     and all ranks' node updates / that time, in MLUPS.  dist: torch.distributed (initialised) or
@@ -290,33 +279,25 @@ def host_cpu():
     return platform.machine()
 
 
-def cpu_baseline(seconds_budget=8.0):
-    """The FP64 oracle as it stands, on the host cores: one thread on a 64 x 32 x 32 sub-box of
-    the channel (same rates, closure, force and walls, Yu route); then one spawned process per
-    host core, each stepping its own copy of a 64^3 sub-box (the value reported: total node
-    updates / wall time); and one thread on the 512^2 D2Q9 power-law cavity (Chai route)."""
+def cpu_baseline(steps, warmup, seconds_budget=8.0):
+    """The FP64 oracle as it stands, on the host cores, on the reference arm's configuration: one
+    spawned process per host core, each stepping its own nx x 32 x 32 sub-box of the channel (same
+    rates, closure, force and walls, Yu route; nx as the reference arm picks it for these steps),
+    for about seconds_budget of timed steps; value = all processes' node updates / the slowest
+    process's timed steps.  Also one thread on the 512^2 D2Q9 power-law cavity (Chai route)."""
     import multiprocessing as mp
 
     import oracle as O
 
     O.lib()  # built once before the workers start
-    nx, ny, nz = 64, 32, 32
-    Gr, f, F = _oracle_channel_box(nx, ny, nz)
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < seconds_budget and steps < 200:
-        f, _ = Gr.step(f, force=F)
-        steps += 1
-    single = nx * ny * nz * steps / (time.perf_counter() - t0) / 1e6
+    dims, rate = reference_subbox(steps, warmup)
+    nodes = dims[0] * dims[1] * dims[2]
+    per = max(1, int(rate * seconds_budget / nodes))  # timed steps per process for ~budget seconds
     cores = os.cpu_count() or 1
-    n64 = 64 ** 3
-    per = max(1, int(single * 1e6 * seconds_budget / n64))  # steps per replica for ~budget seconds
-    ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_replica, [((64, 64, 64), per)] * cores)
-    wall = time.perf_counter() - t0
-    allcore = sum(r[0] for r in res) / wall / 1e6
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_reference_worker, [(dims, 1, per)] * cores)
+    dt = max(r[1] for r in res)
+    allcore = sum(r[0] for r in res) * per / dt / 1e6
     # D2Q9 512^2 lid-driven power-law cavity (n = 0.5), one thread
     L2, U = 512, 0.05
     tau_ref = 0.5 + 3 * U * L2 / 1000.0
@@ -333,10 +314,9 @@ def cpu_baseline(seconds_budget=8.0):
         s9 += 1
     d2q9 = L2 * L2 * s9 / (time.perf_counter() - t0) / 1e6
     return {"value": round(allcore, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": "FP64 oracle, Yu route, channel rates/closure/force/walls: %d processes (one per host core), "
-                      "each %d steps of its own 64^3 sub-box" % (cores, per),
-            "single_thread": {"value": round(single, 4), "unit": "MLUPS",
-                              "sample": "%dx%dx%d sub-box of the channel, %d steps, one thread" % (nx, ny, nz, steps)},
+            "sample": reference_sample(cores, dims) + ", %d timed steps each" % per,
+            "single_thread": {"value": round(rate / 1e6, 4), "unit": "MLUPS",
+                              "sample": "calibration step of a 16x32x16 sub-box of the channel, one thread"},
             "d2q9_512_cavity": {"value": round(d2q9, 4), "unit": "MLUPS",
                                 "sample": "512^2 power-law (n = 0.5) lid cavity, Chai route, %d steps, one thread" % s9},
             "host_cpu": host_cpu()}
@@ -427,7 +407,7 @@ def run_ours(args):
         if not args.no_variants:
             out["variants"] = variants(args, hbm, out["alu_peaks"])
         if world == 1:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(args.steps, args.warmup)
         print(json.dumps(out), flush=True)
     lat.close()
     if dist:
@@ -731,6 +711,23 @@ def _reference_worker(job):
     return Gr.N, time.perf_counter() - t0
 
 
+def reference_subbox(steps, warmup):
+    """The sub-box each host process of the oracle arms steps, ((nx, 32, 32), one thread's rate in
+    node updates per second): nx from a calibration step so that warmup + steps steps take about
+    90 s, at most the channel's 256."""
+    Gc, fc, F = _oracle_channel_box(16, 32, 16)
+    t0 = time.perf_counter()
+    Gc.step(fc, force=F)
+    rate = Gc.N / (time.perf_counter() - t0)
+    nodes = rate * 90.0 / (steps + warmup)
+    return (int(max(1, min(NX, nodes // (32 * 32)))), 32, 32), rate
+
+
+def reference_sample(cores, dims):
+    return ("%d processes (one per host core), each an %dx%dx%d sub-box of the channel (walls at y) per step, "
+            "FP64 oracle, Yu route" % ((cores,) + tuple(dims)))
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores: one spawned process per core, each stepping its
     own nx x 32 x 32 sub-box of the channel (walls at y, same rates, closure and force), nx sized
@@ -744,19 +741,13 @@ def run_reference(args):
     import oracle as O
 
     O.lib()  # built once before the workers start
-    Gc, fc, F = _oracle_channel_box(16, 32, 16)
-    t0 = time.perf_counter()
-    Gc.step(fc, force=F)
-    rate = Gc.N / (time.perf_counter() - t0)
-    nodes = rate * 90.0 / (args.steps + args.warmup)
-    nx = int(max(1, min(NX, nodes // (32 * 32))))
+    dims, _ = reference_subbox(args.steps, args.warmup)
     cores = os.cpu_count() or 1
     with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_reference_worker, [((nx, 32, 32), args.warmup, args.steps)] * cores)
+        res = pool.map(_reference_worker, [(dims, args.warmup, args.steps)] * cores)
     dt = max(r[1] for r in res)
     value = sum(r[0] for r in res) * args.steps / dt / 1e6
-    sample = ("%d processes (one per host core), each an %dx32x32 sub-box of the channel (walls at y) per step, "
-              "FP64 oracle, Yu route" % (cores, nx))
+    sample = reference_sample(cores, dims)
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
