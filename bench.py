@@ -415,6 +415,87 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def slab_lattice(precision, formula, rank, world):
+    """This rank's z-slab of the channel: the 128 planes split evenly over the ranks, halo z faces
+    (the planes of the ranks below and above in the ghost planes), the channel's start."""
+    from paper_1704_07559_gb300 import inputs as I
+    from paper_1704_07559_gb300 import lbm, slab
+
+    z0, z1 = slab.split_planes(NZ, world, rank)
+    lat = lbm.Lattice(19, NX, NY, z1 - z0, rates=RATES, force=[G, 0.0, 0.0], precision=precision, closure="smag",
+                      smag_cs=CS, formula=formula, bc=BC[:4] + ["halo", "halo"])
+    drho, u = I.channel_profile(NX, NY, NZ, u_centre=0.1, noise=0.01, seed=2)
+    planes = np.arange(z0 - 1, z1 + 1) % NZ
+    lat.init(np.take(drho, planes, axis=-3), np.take(u, planes, axis=-3))
+    return lat
+
+
+def run_slab(args):
+    """--decomp slab: one channel cut into z-slabs, one per rank, halos exchanged after every step
+    (NCCL send/recv between the GPUs; one rank exchanges with itself), strong scaling.  The timed
+    region holds the steps and the exchanges; value = the channel's node updates / the slowest
+    rank's time."""
+    import torch
+
+    from paper_1704_07559_gb300 import build, slab
+
+    rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    lat = slab_lattice(args.precision, args.formula, rank, world)
+    own = lat.N // lat.nz * (lat.nz - 2)
+    ex = slab.Slabs(lat, dist)
+    ex.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    s = lat.stream
+    steps0, launches0 = lat.stats()
+    with ClockSampler(local) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        ex.step(args.steps)
+        t1.record(s)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+    launches = lat.stats()[1] - launches0 + 2 * args.steps  # step kernels, and a pack and an unpack per step
+    local_ms = ms
+    ms, value = job_rate(ms, own * args.steps, dist, device="cuda")
+    bpl = BYTES_PER_LUP[args.precision]
+    achieved = bpl * own / (local_ms / args.steps * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": [NX, NY, NZ], "formula": args.formula,
+                      "closure": CLOSURE_NOTE["smag"], "precision": STORAGE_NOTE[args.precision],
+                      "parallelism": "z-slabs over %d rank(s), halos exchanged every step" % world,
+                      "l2": "inputs larger than L2 (two 319 MB population buffers per step, split over the ranks)"},
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+                        "kernel": "k_step<D3Q19,%s,SMAG,%s,force> + halo copies + exchange" % (args.precision,
+                                                                                           args.formula.upper()),
+                        "bytes_per_lup": bpl, "per": "lattice step of this rank's slab, exchange included"},
+           "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    lat.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def fp64_alu_counts():
     """FP64 flops and FP64-pipe instructions per node update of the FP64 Yu-route step kernel,
     from the committed ncu capture (profiles/fp64_alu.json), or None."""
@@ -771,6 +852,9 @@ def main():
                     help="the channel's Smagorinsky closure: implicit (default), lagged or deviatoric closed form")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 15],
                     help="19: the D3Q19 channel (default); 15: the same channel on D3Q15")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="replicas: one channel per rank (default, weak scaling); slab: one channel cut into "
+                         "z-slabs over the ranks, halos exchanged every step (strong scaling)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()
@@ -778,6 +862,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.decomp == "slab":
+        run_slab(args)
     else:
         run_ours(args)
 

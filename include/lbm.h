@@ -28,7 +28,7 @@
  *  - Fields passed in or out are dense component-major arrays: component c of node n at c*N + n,
  *    N = nx*ny*nz.  Strain components are xx, yy, zz, xy, yz, xz in 3D and xx, yy, xy in 2D.
  *  - Faces are numbered -x, +x, -y, +y, -z, +z.  Opposite faces must both be periodic or both
- *    not.  A wall is halfway bounce-back; a moving wall ("lid") adds 2 w_i rho0 (c_i . u_w)/cs^2
+ *    not (and both LBM_HALO, only on z).  A wall is halfway bounce-back; a moving wall ("lid") adds 2 w_i rho0 (c_i . u_w)/cs^2
  *    to the population it reflects; a population that leaves through an edge or corner where
  *    two non-periodic faces meet is reflected without the moving-wall term.
  *  - All calls are asynchronous on the bound stream unless stated otherwise, return LBM_OK or a
@@ -85,6 +85,14 @@ extern "C" {
 #define LBM_PERIODIC 0
 #define LBM_WALL 1
 #define LBM_LID 2
+/* Exchange face of a z-slab (both z faces of a 3D lattice, see lbm_halo_pack): the lattice is one
+ * slab of a larger lattice cut along z, and its neighbouring slabs supply the populations that
+ * enter through these faces.  The context then holds nz + 2 planes: plane 0 and plane nz + 1 are
+ * ghost planes holding the neighbours' boundary populations, planes 1..nz are the slab's own.
+ * Every buffer and field of the context spans all nz + 2 planes (N = nx ny (nz + 2)); steps,
+ * read-outs and sums compute the own planes only; lbm_init fills the ghost planes with what the
+ * first step pulls from them. */
+#define LBM_HALO 3
 
 /* Model parameters (plain data, copied by lbm_create).  |S| = sqrt(2 S:S).  With a closure, S
  * and tau are solved together at each node by fixed-point sweeps on tau from the same
@@ -314,6 +322,31 @@ int lbm_sums_noalloc(int lattice, int nx, int ny, int nz, const lbm_params* p, c
  * After the call the current buffer holds the state after T steps.  Synchronises the stream. */
 int lbm_adjoint_workspace(lbm_ctx* ctx, int T, int seg, int64_t* bytes);
 int lbm_adjoint(lbm_ctx* ctx, int T, int seg, void* work, int64_t work_bytes, double* dLdg, double* loss);
+
+/* Domain decomposition along z (the lattice is cut into slabs of whole z planes, one per context
+ * and usually one per GPU; the paper's method is local in space, Sec. 1 notes the natural
+ * parallelism of the lattice Boltzmann equation).  A context created with bc[4] = bc[5] =
+ * LBM_HALO steps its own planes; between two steps the populations that cross each z face move
+ * to the neighbouring slab:
+ *   lbm_halo_pack    copies, from the current buffer, the post-collision populations with c_z = +1
+ *                    of the top own plane (z = nz) into send_hi and those with c_z = -1 of the
+ *                    bottom own plane (z = 1) into send_lo;
+ *   lbm_halo_unpack  writes recv_lo (the lower neighbour's send_hi) into the populations with
+ *                    c_z = +1 of ghost plane 0 and recv_hi (the upper neighbour's send_lo) into the
+ *                    populations with c_z = -1 of ghost plane nz + 1.
+ * Each halo buffer holds `pops` arrays of nx * ny elements of the storage type (population order:
+ * increasing index among those crossing the face; 5 for D3Q19 and D3Q15), device memory,
+ * caller-owned, `elems` = pops * nx * ny (lbm_halo_layout).  Slab k's upper neighbour is slab
+ * k + 1 (periodically: the lattice as a whole is periodic in z); one slab is its own neighbour.
+ * Stepping then goes step(1), pack, exchange (the caller's: NCCL send/recv between GPUs, or a
+ * copy), unpack, step(1), ...; after lbm_init the ghost planes already hold what the first step
+ * pulls.  With halo faces lbm_step takes n <= 1 (the exchange sits between steps), the watchdog and
+ * the adjoint are not available (LBM_ERR_ARG), and lbm_sums sums the own planes (the lattice's
+ * totals are the sums over the slabs).  Asynchronous on the bound stream.
+ * Errors: LBM_ERR_ARG for a context without halo faces or NULL buffers. */
+int lbm_halo_layout(const lbm_ctx* ctx, int* pops, int64_t* elems);
+int lbm_halo_pack(lbm_ctx* ctx, void* send_lo, void* send_hi);
+int lbm_halo_unpack(lbm_ctx* ctx, const void* recv_lo, const void* recv_hi);
 
 /* Message of the last failed call on ctx (empty if none), owned by the context.  With ctx = NULL:
  * the message of the last failed lbm_create on the calling thread. */

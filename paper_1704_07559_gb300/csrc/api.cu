@@ -17,7 +17,10 @@
 
 struct lbm_ctx {
     int q, d, ns;
-    int nx, ny, nz;
+    int nx, ny, nz;   // nz counts every plane held, ghost planes included
+    int halo;         // 1: both z faces are LBM_HALO (planes 0 and nz - 1 are ghost planes)
+    int z0, nzc;      // planes computed: [z0, z0 + nzc)
+    int hpop_up[5], hpop_dn[5], hpops;  // populations crossing the z faces (c_z = +1 / -1)
     long long N, stride;
     int elem_bytes;
     double rates[19];
@@ -106,6 +109,8 @@ void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
     a->nx = c->nx;
     a->ny = c->ny;
     a->nz = c->nz;
+    a->z0 = c->z0;
+    a->nzc = c->nzc;
     a->stride = c->stride;
     for (int k = 0; k < 19; ++k) {
         a->s[k] = R(k < c->q ? c->rates[k] : 0.0);
@@ -127,7 +132,7 @@ void fill_args(const lbm_ctx* c, lbm::StepArgs<R>* a) {
     int wall = 0, lid = 0;
     for (int f = 0; f < 6; ++f) {
         if (c->d == 2 && f >= 4) continue;
-        if (c->p.bc[f] != LBM_PERIODIC) wall |= 1 << f;
+        if (c->p.bc[f] == LBM_WALL || c->p.bc[f] == LBM_LID) wall |= 1 << f;  // a halo face reads its ghost plane
         if (c->p.bc[f] == LBM_LID) lid |= 1 << f;
         for (int k = 0; k < 3; ++k) a->lid[f][k] = R(c->p.lid_u[f][k]);
     }
@@ -184,7 +189,7 @@ Tag tag_of(int q, int precision) {
 // more than 2^22 nodes, or too few units to keep every resident block busy without waiting; the
 // caller then launches step by step.
 cudaError_t run_stream(lbm_ctx* c, int nsteps) {
-    if (c->p.precision == LBM_FP64 || c->schedule == LBM_SCHEDULE_PER_STEP)
+    if (c->p.precision == LBM_FP64 || c->schedule == LBM_SCHEDULE_PER_STEP || c->halo)
         return cudaErrorNotSupported;
     // automatic schedule: 3D lattices of at most 2^22 nodes (measured on GB300: +7% on a 4.2M-node
     // channel, +17% on a 2.1M-node box, but -8% on a 7.1M-node box, -2% on a 2048^2 and -26% on a
@@ -414,6 +419,7 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 int adjoint_check(lbm_ctx* c, int T, int seg) {
     if (c->q != 19) return fail(c, LBM_ERR_ARG, "lbm_adjoint: D3Q19 only");
+    if (c->halo) return fail(c, LBM_ERR_ARG, "lbm_adjoint: not for a lattice with halo faces");
     if (c->p.precision != LBM_FP32 && c->p.precision != LBM_FP64)
         return fail(c, LBM_ERR_ARG, "lbm_adjoint: FP32 or FP64 populations only");
     if (c->p.closure != LBM_NEWTON && c->p.closure != LBM_SMAG)
@@ -612,6 +618,30 @@ __global__ void k_sums_final(const double* __restrict__ partial, int nblocks, in
 }
 }  // namespace lbm
 
+namespace {
+
+// the halo copy of the current buffer: lo / hi are the halo buffers (send for a pack, receive for
+// an unpack)
+lbm::HaloArgs halo_args(const lbm_ctx* c, void* lo, void* hi) {
+    lbm::HaloArgs h;
+    std::memset(&h, 0, sizeof(h));
+    h.buf = static_cast<char*>(c->buf[c->cur]);
+    h.pitch = c->stride * c->elem_bytes;
+    h.plane = (long long)c->nx * c->ny;
+    h.pops = c->hpops;
+    for (int k = 0; k < c->hpops; ++k) {
+        h.up[k] = c->hpop_up[k];
+        h.dn[k] = c->hpop_dn[k];
+    }
+    h.z_lo = c->z0;                // bottom own plane
+    h.z_hi = c->z0 + c->nzc - 1;   // top own plane
+    h.lo = static_cast<char*>(lo);
+    h.hi = static_cast<char*>(hi);
+    return h;
+}
+
+}  // namespace
+
 extern "C" {
 
 void lbm_default_params(lbm_params* p) {
@@ -652,20 +682,34 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     c->ns = lattice == LBM_D2Q9 ? 3 : 6;
     if (nx < 1 || ny < 1 || nz < 1) return bad("dims");
     if (c->d == 2 && nz != 1) return bad("nz");
-    if (ny > 65535 || nz > 65535) return bad("ny/nz");
-    const long long N = (long long)nx * ny * nz;
-    if (N >= (1LL << 31)) return bad("N");
-    c->nx = nx;
-    c->ny = ny;
-    c->nz = nz;
-    c->N = N;
-    c->stride = (N + 127) / 128 * 128;
     if (!rates) return bad("rates");
     if (pin)
         c->p = *pin;
     else
         lbm_default_params(&c->p);
     lbm_params& p = c->p;
+    // halo faces (z only, both): the context holds a ghost plane beyond each
+    c->halo = (c->d == 3 && p.bc[4] == LBM_HALO && p.bc[5] == LBM_HALO) ? 1 : 0;
+    const int nzb = c->halo ? nz + 2 : nz;
+    if (ny > 65535 || nzb > 65535) return bad("ny/nz");
+    const long long N = (long long)nx * ny * nzb;
+    if (N >= (1LL << 31)) return bad("N");
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nzb;
+    c->z0 = c->halo ? 1 : 0;
+    c->nzc = nz;
+    c->N = N;
+    c->stride = (N + 127) / 128 * 128;
+    c->hpops = 0;
+    for (int i = 0; i < c->q && c->d == 3; ++i) {
+        const int cz = c->q == 19 ? lbm::D3Q19::c(i, 2) : lbm::D3Q15::c(i, 2);
+        if (cz == 1) c->hpop_up[c->hpops++] = i;
+    }
+    for (int i = 0, k = 0; i < c->q && c->d == 3; ++i) {
+        const int cz = c->q == 19 ? lbm::D3Q19::c(i, 2) : lbm::D3Q15::c(i, 2);
+        if (cz == -1) c->hpop_dn[k++] = i;
+    }
     for (int k = 0; k < c->q; ++k) {
         const double s = rates[k];
         if (!is_finite(s)) return bad("rate");
@@ -704,6 +748,10 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     if (!is_finite(p.pl_tol)) return bad("pl_tol");
     for (int a = 0; a < c->d; ++a) {
         const int f0 = p.bc[2 * a], f1 = p.bc[2 * a + 1];
+        if (a == 2 && (f0 == LBM_HALO || f1 == LBM_HALO)) {
+            if (f0 != f1) return bad("bc pair");
+            continue;
+        }
         if (f0 < LBM_PERIODIC || f0 > LBM_LID || f1 < LBM_PERIODIC || f1 > LBM_LID) return bad("bc");
         if ((f0 == LBM_PERIODIC) != (f1 == LBM_PERIODIC)) return bad("bc pair");
     }
@@ -721,7 +769,7 @@ int lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, const double*
     // library-owned scratch for the global sums and the multi-step launch
     cudaError_t e = cudaMalloc(&c->partial, sizeof(double) * (size_t)lbm::SUM_BLOCKS * (1 + c->d));
     if (e == cudaSuccess) e = cudaMalloc(&c->result, sizeof(double) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->sync, sizeof(int) * (2 + (size_t)nz * c->stream_tiles));
+    if (e == cudaSuccess) e = cudaMalloc(&c->sync, sizeof(int) * (2 + (size_t)c->nz * c->stream_tiles));
     if (e == cudaSuccess) e = cudaMemset(c->sync, 0, sizeof(int));
     if (e != cudaSuccess) {
         snprintf(create_err, sizeof(create_err), "lbm_create: scratch allocation failed: %s", cudaGetErrorString(e));
@@ -764,6 +812,7 @@ int lbm_set_schedule(lbm_ctx* c, int schedule) {
 int lbm_set_watchdog(lbm_ctx* c, int every, double tol) {
     if (!c) return LBM_ERR_ARG;
     if (every < 0) return fail(c, LBM_ERR_ARG, "lbm_set_watchdog: every < 0");
+    if (every > 0 && c->halo) return fail(c, LBM_ERR_ARG, "lbm_set_watchdog: a slab's own totals change by the flux through its halo faces");
     if (every > 0 && !(tol >= 0.0 && is_finite(tol))) return fail(c, LBM_ERR_ARG, "lbm_set_watchdog: tol");
     c->watch_every = every;
     c->watch_tol = tol;
@@ -875,6 +924,8 @@ int lbm_step(lbm_ctx* c, int n) {
     int rc = check_bound(c);
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_ERR_ARG, "lbm_step: n < 0");
+    if (c->halo && n > 1)
+        return fail(c, LBM_ERR_ARG, "lbm_step: a lattice with halo faces takes one step per call (exchange between steps)");
     if (c->watch_every > 0 && n > 0) return step_watched(c, n);
     long long launches = 0;
     cudaError_t e = advance(c, n, &launches);
@@ -934,6 +985,34 @@ int lbm_set_state(lbm_ctx* c, const void* src) {
                         : cudaMemcpy2DAsync(c->buf[c->cur], pitch, src, row, row, c->q, cudaMemcpyDefault, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_state");
     c->watch_ref_ok = 0;
+    return LBM_OK;
+}
+
+int lbm_halo_layout(const lbm_ctx* c, int* pops, int64_t* elems) {
+    if (!c || !c->halo) return LBM_ERR_ARG;
+    if (pops) *pops = c->hpops;
+    if (elems) *elems = (int64_t)c->hpops * c->nx * c->ny;
+    return LBM_OK;
+}
+
+int lbm_halo_pack(lbm_ctx* c, void* send_lo, void* send_hi) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!c->halo) return fail(c, LBM_ERR_ARG, "lbm_halo_pack: the lattice has no halo faces");
+    if (!send_lo || !send_hi) return fail(c, LBM_ERR_ARG, "lbm_halo_pack: two send buffers are required");
+    cudaError_t e = lbm::halo_copy(halo_args(c, send_lo, send_hi), 1, c->elem_bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_halo_pack");
+    return LBM_OK;
+}
+
+int lbm_halo_unpack(lbm_ctx* c, const void* recv_lo, const void* recv_hi) {
+    int rc = check_bound(c);
+    if (rc) return rc;
+    if (!c->halo) return fail(c, LBM_ERR_ARG, "lbm_halo_unpack: the lattice has no halo faces");
+    if (!recv_lo || !recv_hi) return fail(c, LBM_ERR_ARG, "lbm_halo_unpack: two receive buffers are required");
+    cudaError_t e = lbm::halo_copy(halo_args(c, const_cast<void*>(recv_lo), const_cast<void*>(recv_hi)), 0,
+                                   c->elem_bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_halo_unpack");
     return LBM_OK;
 }
 

@@ -16,12 +16,12 @@ cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s
     if constexpr (sizeof(ST) == 2) {
         if (!a.readout && a.nx % 2 == 0) {
             dim3 g, b;
-            lattice_grid(a.nx / 2, a.ny, a.nz, &g, &b);
+            lattice_grid(a.nx / 2, a.ny, a.nzc, &g, &b);
             return launch_pdl(k_step_pair_seq<L, ST, C, F, FO>, g, b, s, a);
         }
     }
     dim3 g, b;
-    lattice_grid(a.nx, a.ny, a.nz, &g, &b);
+    lattice_grid(a.nx, a.ny, a.nzc, &g, &b);
     return launch_pdl(k_step<L, ST, C, F, FO>, g, b, s, a);
 }
 
@@ -67,7 +67,7 @@ template <class L, class ST>
 cudaError_t launch_init(const StepArgs<double>& a, int closure, const double* drho, const double* u, const double* gu,
                         const typename Store<ST>::R* ffield, typename Store<ST>::R* tau_field, cudaStream_t s) {
     dim3 g, b;
-    lattice_grid(a.nx, a.ny, a.nz, &g, &b);
+    lattice_grid(a.nx, a.ny, a.nzc, &g, &b);
     k_init<L, ST><<<g, b, 0, s>>>(a, closure, drho, u, gu, ffield, tau_field);
     return cudaGetLastError();
 }

@@ -50,6 +50,24 @@ struct StreamCtl {
 
 constexpr int SUM_BLOCKS = 608;  // 4 blocks per SM on 152 SMs; partial rows in scratch
 
+// The populations crossing the z faces of a slab (k_halo.cu): population up[k] (c_z = +1) of the
+// top own plane z_hi and population dn[k] (c_z = -1) of the bottom own plane z_lo, each plane
+// `plane` elements; lo / hi hold pops * plane elements.  A pack copies the own planes into hi (up)
+// and lo (dn); an unpack copies lo into population up[k] of ghost plane z_lo - 1 and hi into
+// population dn[k] of ghost plane z_hi + 1.
+struct HaloArgs {
+    char* buf;         // population buffer
+    long long pitch;   // bytes between population arrays
+    long long plane;   // elements of one z plane (nx ny)
+    int pops;          // populations crossing each face
+    int up[5], dn[5];
+    int z_lo, z_hi;    // bottom and top own planes
+    char* lo;
+    char* hi;
+};
+// pack (1) or unpack (0), elements of elem_bytes bytes
+cudaError_t halo_copy(const HaloArgs& h, int pack, int elem_bytes, cudaStream_t s);
+
 #define LBM_DECLARE_ENTRY(TAG, R)                                                                         \
     cudaError_t step_##TAG(const StepArgs<R>& a, int closure, int formula, int force, cudaStream_t s);   \
     cudaError_t init_##TAG(const StepArgs<double>& a, int closure, const double* drho, const double* u, \

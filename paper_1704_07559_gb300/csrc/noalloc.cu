@@ -57,6 +57,8 @@ void fill(lbm::StepArgs<R>* a, int q, int nx, int ny, int nz, const lbm_params* 
     a->nx = nx;
     a->ny = ny;
     a->nz = nz;
+    a->z0 = 0;
+    a->nzc = nz;
     a->stride = stride;
     a->src = f;
     for (int i = 0; i < q; ++i) a->srcp[i] = static_cast<const char*>(f) + (size_t)i * stride * elem;

@@ -35,6 +35,7 @@
 
 #include "lattice.cuh"
 
+
 namespace lbm {
 
 enum { CL_NEWTON = 0, CL_SMAG = 1, CL_POWERLAW = 2, CL_SMAG_LAGGED = 3, CL_SMAG_DEV = 4 };
@@ -161,6 +162,7 @@ __device__ __forceinline__ double c_pow(double x, double y) { return pow(x, y); 
 template <class RS>
 struct StepArgs {
     int nx, ny, nz;
+    int z0, nzc;           // planes computed: [z0, z0 + nzc) (all, or the owned planes between halo planes)
     int readout;           // 0: step (write f*); 1: write S/tau/drho/u of the pre-collision state
     long long stride;      // elements between population arrays
     const void* src;       // post-collision buffer of the previous step
@@ -1290,7 +1292,7 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
     pdl_release();  // every block has started: the next step may be scheduled into freed slots
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = blockIdx.z + a.z0;
     if (x >= a.nx || y >= a.ny) return;
     typename Store<ST>::R f[L::Q];
     pull<L, ST>(a, x, y, z, f);
@@ -1307,7 +1309,7 @@ __global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typenam
     pdl_release();
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = blockIdx.z + a.z0;
     if (x >= a.nx || y >= a.ny) return;
     F2 f2[L::Q];
     pull2<L, ST>(a, x, y, z, f2);
@@ -1331,7 +1333,7 @@ __global__ void __launch_bounds__(128) k_init(const StepArgs<double> a, int clos
     constexpr int Q = L::Q, D = L::D;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z = blockIdx.z + a.z0;
     if (x >= a.nx || y >= a.ny) return;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long N = (long long)nx * ny * nz;  // component offsets (up to 8N) exceed 2^31 on big grids
@@ -1468,10 +1470,10 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename St
     using R = typename Store<ST>::R;
     constexpr int D = L::D;
     const long long N = (long long)a.nx * a.ny * a.nz;  // component offsets c*N exceed 2^31 on big grids
-    const int rows = a.ny * a.nz;
+    const int rows = a.ny * a.nzc;  // the computed planes only (a halo plane belongs to a neighbour)
     Comp<R> acc[1 + D];
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int y = r % a.ny, z = r / a.ny;
+        const int y = r % a.ny, z = r / a.ny + a.z0;
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             R f[L::Q];
             pull<L, ST>(a, x, y, z, f);
@@ -1482,7 +1484,7 @@ __global__ void __launch_bounds__(SUM_THREADS) k_sums(const StepArgs<typename St
                 m0 += f[i];
                 sfor<D>([&](auto d) { mj[d] = cadd<L::c(CV(i), CV(d))>(mj[d], f[i]); });
             });
-            const int n = r * a.nx + x;
+            const int n = (z * a.ny + y) * a.nx + x;
             acc[0].add(m0);
 #pragma unroll
             for (int d = 0; d < D; ++d)

@@ -21,7 +21,7 @@ D2Q9, D3Q15, D3Q19 = 9, 15, 19
 PRECISION = {"fp64": 0, "fp32": 1, "fp16s": 2, "bf16s": 3}
 CLOSURE = {"newton": 0, "smag": 1, "powerlaw": 2, "smag_lagged": 3, "smag_dev": 4}
 FORMULA = {"yu": 0, "chai": 1}
-BC = {"periodic": 0, "wall": 1, "lid": 2}
+BC = {"periodic": 0, "wall": 1, "lid": 2, "halo": 3}
 SCHEDULE = {"auto": 0, "per_step": 1, "stream": 2, "stall_check": 3}
 STORAGE_DTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}
 ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_STATE",
@@ -29,7 +29,7 @@ ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NOMEM", -4: "LBM_E
 API = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_layout", "lbm_bind", "lbm_bind_tau", "lbm_init",
        "lbm_step", "lbm_strain_rate", "lbm_macroscopic", "lbm_sums", "lbm_get_state", "lbm_set_state", "lbm_last_error",
        "lbm_sums_noalloc", "lbm_adjoint_workspace", "lbm_adjoint", "lbm_set_schedule", "lbm_status",
-       "lbm_stats", "lbm_set_watchdog"]
+       "lbm_stats", "lbm_set_watchdog", "lbm_halo_layout", "lbm_halo_pack", "lbm_halo_unpack"]
 
 
 class LBMError(RuntimeError):
@@ -85,6 +85,9 @@ def lib():
     L.lbm_set_schedule.argtypes = [vp, ctypes.c_int]
     L.lbm_status.argtypes = [vp]
     L.lbm_set_watchdog.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    L.lbm_halo_layout.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_halo_pack.argtypes = [vp, vp, vp]
+    L.lbm_halo_unpack.argtypes = [vp, vp, vp]
     L.lbm_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_int, vp, vp]
     L.lbm_macroscopic.argtypes = [vp, vp, vp]
@@ -117,8 +120,10 @@ class Lattice:
 
     rates: q relaxation rates (conserved entries 0, viscous entries 1/tau0).  force: uniform
     body-force density (d values) or None.  force_field: a (d, nz, ny, nx) tensor of the compute
-    dtype (kept referenced) or None.  bc: 6 face kinds ('periodic' | 'wall' | 'lid'), faces
-    -x, +x, -y, +y, -z, +z; lid_u: {face index: (ux, uy, uz)}.
+    dtype (kept referenced) or None.  bc: 6 face kinds ('periodic' | 'wall' | 'lid' | 'halo'),
+    faces -x, +x, -y, +y, -z, +z; lid_u: {face index: (ux, uy, uz)}.  With 'halo' z faces (a slab
+    of a lattice cut along z, see slab.py) nz counts the slab's own planes and every array of the
+    lattice spans nz + 2 planes, the first and last being ghost planes.
     """
 
     def __init__(self, lattice, nx, ny, nz=1, rates=None, force=None, precision="fp32", closure="newton",
@@ -129,7 +134,10 @@ class Lattice:
         self.q = int(lattice)
         self.d = 2 if self.q == D2Q9 else 3
         self.ns = 3 if self.q == D2Q9 else 6
-        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        bc = list(bc) if bc is not None else ["periodic"] * 6
+        bc += ["periodic"] * (6 - len(bc))  # 2D lattices may give only the four x / y faces
+        self.halo = bc[4] == "halo" and bc[5] == "halo"
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz) + (2 if self.halo else 0)
         self.N = self.nx * self.ny * self.nz
         self.shape = (self.nz, self.ny, self.nx)
         self.device = torch.device(device)
@@ -139,8 +147,6 @@ class Lattice:
         p.formula = FORMULA[formula]
         p.smag_iters = smag_iters
         p.pl_max_iter = pl_max_iter
-        bc = list(bc) if bc is not None else ["periodic"] * 6
-        bc += ["periodic"] * (6 - len(bc))  # 2D lattices may give only the four x / y faces
         for f in range(6):
             p.bc[f] = BC[bc[f]] if isinstance(bc[f], str) else int(bc[f])
         p.force_field = 1 if force_field is not None else 0
@@ -161,7 +167,8 @@ class Lattice:
         if force is not None:
             fv = (ctypes.c_double * 3)(*([float(v) for v in force] + [0.0] * (3 - len(force))))
         ctx = ctypes.c_void_p()
-        rc = L.lbm_create(ctypes.byref(ctx), self.q, self.nx, self.ny, self.nz, r, fv, ctypes.byref(p))
+        rc = L.lbm_create(ctypes.byref(ctx), self.q, self.nx, self.ny, self.nz - (2 if self.halo else 0), r, fv,
+                          ctypes.byref(p))
         if rc != 0:
             raise LBMError(rc, L.lbm_last_error(None).decode())
         self.ctx = ctx
@@ -283,6 +290,22 @@ class Lattice:
         self._check(L.lbm_adjoint(self.ctx, int(T), seg, ctypes.c_void_p(work.data_ptr() + off), nbytes.value,
                                   _ptr(grad), ctypes.byref(loss)))
         return loss.value, grad
+
+    def halo_layout(self):
+        """(crossing populations per z face, elements per halo buffer) of a lattice with halo faces."""
+        pops, elems = ctypes.c_int(), ctypes.c_int64()
+        self._check(lib().lbm_halo_layout(self.ctx, ctypes.byref(pops), ctypes.byref(elems)))
+        return pops.value, elems.value
+
+    def halo_pack(self, send_lo, send_hi):
+        """Copy the populations leaving through the lower / upper z face into two device tensors."""
+        self._check(lib().lbm_halo_pack(self.ctx, _ptr(send_lo), _ptr(send_hi)))
+        return self
+
+    def halo_unpack(self, recv_lo, recv_hi):
+        """Write the lower / upper neighbours' outgoing populations into the ghost planes."""
+        self._check(lib().lbm_halo_unpack(self.ctx, _ptr(recv_lo), _ptr(recv_hi)))
+        return self
 
     def set_state(self, f):
         f = f.to(dtype=self.storage_dtype).contiguous()

@@ -83,6 +83,10 @@ def create(L, lattice=19, dims=(8, 8, 8), rates=None, mutate=None):
     dict(mutate=lambda p: (setattr(p, "precision", 2), setattr(p, "closure", 3))),  # 16-bit: lagged
     dict(mutate=lambda p: (setattr(p, "precision", 3), setattr(p, "closure", 4))),  # 16-bit: deviatoric
     dict(rates=D3[:13] + [1.2] + D3[14:], mutate=lambda p: (setattr(p, "formula", 1), setattr(p, "closure", 3))),
+    dict(mutate=lambda p: p.bc.__setitem__(4, 3)),                         # one halo z face
+    dict(mutate=lambda p: (p.bc.__setitem__(0, 3), p.bc.__setitem__(1, 3))),  # halo faces on x
+    dict(mutate=lambda p: (p.bc.__setitem__(4, 3), p.bc.__setitem__(5, 1))),  # halo with a wall
+    dict(dims=(8, 8, 65534), mutate=lambda p: (p.bc.__setitem__(4, 3), p.bc.__setitem__(5, 3))),  # nz + 2 planes
 ])
 def test_create_rejects_bad_arguments(L, case):
     rc, ctx = create(L, **case)
@@ -117,6 +121,19 @@ def test_null_context_calls_fail_cleanly(L):
     assert L.lbm_status(None) == -1
     assert L.lbm_stats(None, None, None) == -1
     assert L.lbm_set_watchdog(None, 1, 1e-6) == -1
+    assert L.lbm_halo_layout(None, None, None) == -1
+    assert L.lbm_halo_pack(None, None, None) == -1
+    assert L.lbm_halo_unpack(None, None, None) == -1
+
+
+def test_halo_faces_pass_the_host_checks(L):
+    """Both z faces LBM_HALO on D3Q19 and D3Q15 pass the host checks (then need a GPU for the
+    context's scratch); on D2Q9 the z faces are ignored."""
+    for lattice in (19, 15):
+        rc, ctx = create(L, lattice=lattice, mutate=lambda p: (p.bc.__setitem__(4, 3), p.bc.__setitem__(5, 3)))
+        assert rc in (0, -2, -3)
+        if rc == 0:
+            L.lbm_destroy(ctx)
 
 
 def test_noalloc_rejects_bad_arguments_before_any_cuda_call(L):
@@ -177,6 +194,7 @@ def test_binding_constants_match_the_header():
     assert lbm.PRECISION == {"fp64": cl["LBM_FP64"], "fp32": cl["LBM_FP32"], "fp16s": cl["LBM_FP16S"],
                              "bf16s": cl["LBM_BF16S"]}
     assert lbm.FORMULA == {"yu": cl["LBM_YU"], "chai": cl["LBM_CHAI"]}
-    assert lbm.BC == {"periodic": cl["LBM_PERIODIC"], "wall": cl["LBM_WALL"], "lid": cl["LBM_LID"]}
+    assert lbm.BC == {"periodic": cl["LBM_PERIODIC"], "wall": cl["LBM_WALL"], "lid": cl["LBM_LID"],
+                      "halo": cl["LBM_HALO"]}
     errs = header_constants("LBM_ERR_")
     assert {v: k for k, v in errs.items()} == {k: v for k, v in lbm.ERRORS.items()}

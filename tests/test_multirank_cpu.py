@@ -28,7 +28,7 @@ def _rank(rank, world, port, times, updates, out):
 
 def test_job_rate_takes_the_slowest_rank_over_two_gloo_ranks():
     times, updates = [12.5, 20.0], 4_000_000
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(2, free_port(), times, updates, out), nprocs=2, join=True)
         res = dict(out)
