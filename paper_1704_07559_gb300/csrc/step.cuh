@@ -306,11 +306,65 @@ struct Xf {
     static __device__ __forceinline__ void backward(const R (&D)[L::Q], R (&out)[L::Q]) {
         back_transform<L, USE>(D, out);
     }
+    template <uint32_t USE, class R>
+    static __device__ __forceinline__ void backward_eo(const R (&D)[L::Q], R& E0, R (&E)[L::NP], R (&O)[L::NP]) {
+        back_transform_eo<L, USE>(D, E0, E, O);
+    }
 };
 
 template <>
 struct Xf<D3Q19> {
     // pair order: x (1,2), y (3,4), z (5,6), (7,10), (8,9), (11,14), (12,13), (15,18), (16,17)
+
+    // Even and odd parts of out_i = sum_k T_ki a_k (as back_transform_eo) for the two masks of the
+    // Chai route, sharing partial sums between pairs: the non-conserved non-viscous moments
+    // (1, 2, 4, 6, 8, 10, 12, 16, 17, 18) and the viscous moments (9, 11, 13, 14, 15, all even).
+    // Other masks use the generic form.
+    template <uint32_t USE, class R>
+    static __device__ __forceinline__ void backward_eo(const R (&a)[19], R& E0, R (&E)[9], R (&O)[9]) {
+        constexpr uint32_t FIXED = mask_nonconserved<D3Q19>() & ~mask_viscous<D3Q19>();
+        constexpr uint32_t VISC = mask_viscous<D3Q19>();
+        if constexpr (USE == FIXED) {
+            E0 = fma(R(12.0f), a[2], R(-30.0f) * a[1]);
+            const R B1 = fma(R(-4.0f), a[2], R(-11.0f) * a[1]);  // axis pairs
+            const R B2 = fma(R(8.0f), a[1], a[2]);               // edge pairs
+            const R s = a[10] + a[12], t = a[10] - a[12];
+            E[0] = fma(R(-4.0f), a[10], B1);
+            E[1] = fma(R(2.0f), t, B1);
+            E[2] = fma(R(2.0f), s, B1);
+            E[3] = E[4] = B2 + s;                                // xy edges
+            E[5] = E[6] = B2 + t;                                // xz edges
+            E[7] = E[8] = fma(R(-2.0f), a[10], B2);             // yz edges
+            O[0] = R(-4.0f) * a[4];
+            O[1] = R(-4.0f) * a[6];
+            O[2] = R(-4.0f) * a[8];
+            const R u1 = a[4] + a[16], v1 = a[6] - a[17];        // (7,10), (8,9)
+            O[3] = v1 + u1;
+            O[4] = v1 - u1;
+            const R u2 = a[4] - a[16], v2 = a[8] + a[18];        // (11,14), (12,13)
+            O[5] = v2 + u2;
+            O[6] = v2 - u2;
+            const R u3 = a[6] + a[17], v3 = a[8] - a[18];        // (15,18), (16,17)
+            O[7] = v3 + u3;
+            O[8] = v3 - u3;
+        } else if constexpr (USE == VISC) {
+            E0 = R(0.0f);
+            const R p = a[9] + a[11], m = a[9] - a[11], t = R(-2.0f) * a[9];
+            E[0] = R(2.0f) * a[9];
+            E[1] = -m;
+            E[2] = -p;
+            E[3] = p + a[13];
+            E[4] = p - a[13];
+            E[5] = m + a[15];
+            E[6] = m - a[15];
+            E[7] = t + a[14];
+            E[8] = t - a[14];
+            sfor<9>([&](auto q) { O[q] = R(0.0f); });
+        } else {
+            back_transform_eo<D3Q19, USE>(a, E0, E, O);
+        }
+    }
+
     template <class R>
     static __device__ __forceinline__ void forward(R f0, const R (&P)[9], const R (&D)[9], R (&m)[19]) {
         const R Exy = P[3] + P[4], Exz = P[5] + P[6], Eyz = P[7] + P[8];
@@ -448,6 +502,41 @@ struct Xf<D3Q15> {
         m[12] = c + d;
         m[13] = c - d;
         m[14] = w - x;
+    }
+
+    // Even and odd parts of out_i = sum_k T_ki a_k for the Chai route's two masks: the
+    // non-conserved non-viscous moments (1, 2, 4, 6, 8, 14) and the viscous moments (9..13, all
+    // even), with the corner pairs as butterflies; other masks use the generic form.
+    template <uint32_t USE, class R>
+    static __device__ __forceinline__ void backward_eo(const R (&a)[15], R& E0, R (&E)[7], R (&O)[7]) {
+        constexpr uint32_t FIXED = mask_nonconserved<D3Q15>() & ~mask_viscous<D3Q15>();
+        constexpr uint32_t VISC = mask_viscous<D3Q15>();
+        if constexpr (USE == FIXED) {
+            E0 = fma(R(16.0f), a[2], R(-2.0f) * a[1]);
+            E[0] = E[1] = E[2] = fma(R(-4.0f), a[2], -a[1]);   // axis pairs
+            E[3] = E[4] = E[5] = E[6] = a[1] + a[2];           // corner pairs
+            O[0] = R(-4.0f) * a[4];
+            O[1] = R(-4.0f) * a[6];
+            O[2] = R(-4.0f) * a[8];
+            const R p = a[8] + a[6], m = a[8] - a[6], c = a[4] + a[14], d = a[4] - a[14];
+            O[3] = p + c;  // (7,14): c = (1, 1, 1)
+            O[4] = p - c;  // (8,13): (-1, 1, 1)
+            O[5] = m + d;  // (9,12): (1, -1, 1)
+            O[6] = m - d;  // (10,11): (-1, -1, 1)
+        } else if constexpr (USE == VISC) {
+            E0 = R(0.0f);
+            E[0] = R(2.0f) * a[9];
+            E[1] = a[10] - a[9];
+            E[2] = -(a[9] + a[10]);
+            const R s1 = a[11] + a[13], s2 = a[11] - a[13];
+            E[3] = a[12] + s1;
+            E[4] = a[12] - s1;
+            E[5] = -(a[12] + s2);
+            E[6] = s2 - a[12];
+            sfor<7>([&](auto q) { O[q] = R(0.0f); });
+        } else {
+            back_transform_eo<D3Q15, USE>(a, E0, E, O);
+        }
     }
 
     // out_i = sum_k T_ki a_k for every non-conserved a_k (with CONS also a_3, a_5, a_7); other
@@ -1242,8 +1331,8 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
             // are all even, so Omega_v has no odd part, and S needs only the even parts
             static_assert(viscous_moments_even<L>(), "viscous moments must be even");
             R Ef0, Ef[NP], Of[NP], Ev0, Ev[NP], Ovd[NP];
-            back_transform_eo<L, mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Ef0, Ef, Of);
-            back_transform_eo<L, mask_viscous<L>()>(Dv, Ev0, Ev, Ovd);
+            Xf<L>::template backward_eo<mask_nonconserved<L>() & ~mask_viscous<L>()>(Df, Ef0, Ef, Of);
+            Xf<L>::template backward_eo<mask_viscous<L>()>(Dv, Ev0, Ev, Ovd);
             R Nf[NS], Nv[NS], A[NS], B[NS];
             contract_even<L>(Ef, Nf);
             contract_even<L>(Ev, Nv);
@@ -1299,6 +1388,16 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
     step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, (z * a.ny + y) * a.nx + x);
 }
 
+// The collisions of the two nodes of a shared pull (node, node + 1), one after the other.
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__device__ __forceinline__ void step_two(const StepArgs<typename Store<ST>::R>& a, const F2 (&f2)[L::Q], int node) {
+    float f[L::Q];
+    sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
+    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node);
+    sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
+    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
+}
+
 // Two x-adjacent nodes per thread that share the pull (paired loads where c_x = 0, adjacent
 // scalar loads otherwise) and then collide one after the other in scalar arithmetic.  Bound to 7
 // resident blocks per SM (72 registers; a few spilled values): measured faster than the 80
@@ -1314,11 +1413,7 @@ __global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typenam
     F2 f2[L::Q];
     pull2<L, ST>(a, x, y, z, f2);
     const int node = (z * a.ny + y) * a.nx + x;
-    float f[L::Q];
-    sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node);
-    sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
+    step_two<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, node);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -77,12 +77,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R
             for (int x = 2 * (int)threadIdx.x; x < a.nx; x += 2 * (int)blockDim.x) {
                 F2 f2[L::Q];
                 pull2<L, ST, true>(a, x, y, z, f2);
-                const int node = (z * a.ny + y) * a.nx + x;
-                R f[L::Q];
-                sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
-                step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node);
-                sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
-                step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
+                step_two<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, (z * a.ny + y) * a.nx + x);
             }
         } else {
             for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
