@@ -2,10 +2,10 @@
 times (its own workload constructors build every lattice here).
 
 The headline channel (256 x 128 x 128) is compared whole: every node's read-outs and populations
-against the oracle run over z-slabs in parallel host processes.  The other workloads (the 512^3
-box, the 4096^2 cavity) and the channel's variants are compared at sampled nodes: after a few GPU
-steps, the strain-rate read-outs and the next step are compared with the FP64 oracle at sampled
-nodes: corners, face and edge centres, and seeded random nodes.  For each
+against the oracle run over z-slabs in parallel host processes; so is the 4096^2 D2Q9 cavity (the
+oracle over y-slabs).  The 512^3 box and the channel's variants are compared at sampled nodes:
+after a few GPU steps, the strain-rate read-outs and the next step are compared with the FP64
+oracle at corners, face and edge centres, and seeded random nodes.  For each
 sampled node the oracle gets the node's neighbourhood, a patch of up to 3 x 3 x 3 nodes cut from
 the GPU's populations (converted exactly to float64) with the workload's boundary kind on every
 face the node touches, and computes that node's collision on its own (or_node).  Bars are those
@@ -221,6 +221,44 @@ def test_cavity_4096_sampled(nidx, formula):
                       sorted(set(nodes)), lid={3: (U, 0.0, 0.0)}, pl=(nidx, K))
     assert np.abs(S).max() > 1e-4  # the lid layer shears
     lat.close()
+
+
+@pytest.mark.parametrize("nidx,formula", [(0.5, "chai"), (1.5, "yu")])
+def test_cavity_4096_whole_array(nidx, formula):
+    """The D2Q9 power-law lid-driven cavity at its full 4096^2 size, every node: after 300 steps
+    (one launch per step, as the bench runs it), the read-outs of that state by both formulas
+    (Chai's and the Yu-type formula of the Sec. 5.4 procedure) and tau, and the populations after
+    one more step, against the oracle run over y-slabs in one spawned process per host core (the
+    cavity's walls and lid kept where a slab reaches them).  Same bars as the channel's
+    whole-array test."""
+    from oracle import slabs
+
+    t = TOL["fp32"]
+    lat = bench.cavity_lattice(4096, nidx, formula)
+    lat.step(300)
+    f300 = lat.get_state().to(torch.float64).cpu().numpy()
+    reads = {fm: [x.to(torch.float64).cpu().numpy() for x in lat.strain_rate(fm, with_tau=True)]
+             for fm in ("yu", "chai")}
+    lat.step(1)
+    f301 = lat.get_state().to(torch.float64).cpu().numpy()
+    lat.close()
+    U = bench.CAVITY_U
+    K = U ** (2 - nidx) * 4096 ** nidx / bench.CAVITY_RE
+    tau_ref = 0.5 + 3 * U * 4096 / bench.CAVITY_RE
+    lid = [[0.0, 0.0, 0.0] for _ in range(6)]
+    lid[3] = [U, 0.0, 0.0]
+    kw = dict(q=9, rates=[0, 1.19, 1.4, 0, 1.2, 0, 1.2, 1 / tau_ref, 1 / tau_ref], closure=O.POWERLAW,
+              formula=O.YU if formula == "yu" else O.CHAI, bc=[O.WALL, O.WALL, O.WALL, O.LID, O.PERIODIC, O.PERIODIC],
+              lid_u=lid, pl_n=nidx, pl_k=K, pl_tol=1e-7)
+    fo, ro = slabs.run(kw, f300, steps=1, readouts=("yu", "chai"), axis="y")
+    for fm in ("yu", "chai"):
+        S, tau = reads[fm]
+        assert relerr(S, ro[fm][0]) <= t["S"], (fm, relerr(S, ro[fm][0]))
+        assert relerr(tau, ro[fm][1]) <= t["S"], (fm, relerr(tau, ro[fm][1]))
+    assert np.abs(reads["chai"][0]).max() > 1e-4  # the lid layer shears
+    err = np.abs(f301 - fo)
+    bound = t["f"] * np.abs(fo).max()
+    assert np.all(err <= bound), (err.max() / np.abs(fo).max())
 
 
 def test_tgv_32_fp64_whole_trajectory():
