@@ -124,6 +124,10 @@ struct Store<__half> {
     static __device__ __forceinline__ R ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ R ldc(const __half* p) { return __half2float(__ldcg(p)); }
     static __device__ __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(v); }
+    // aligned pair p[0] = lo, p[1] = hi (p 4-byte aligned), each rounded to nearest as st does
+    static __device__ __forceinline__ void st2(__half* p, R lo, R hi) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(lo, hi);
+    }
     static __device__ __forceinline__ F2 ld2(const __half* p) {
         return F2(__half22float2(__ldg(reinterpret_cast<const __half2*>(p))));
     }
@@ -137,6 +141,9 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ R ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ R ldc(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st2(__nv_bfloat16* p, R lo, R hi) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+    }
     static __device__ __forceinline__ F2 ld2(const __nv_bfloat16* p) {
         return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p))));
     }
@@ -1185,10 +1192,10 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 // by the chosen route, closure, relaxation, force, and either the store of f* or (readout) the
 // store of S, tau, drho and u.  ds shifts the populations' destination by that many elements (a
 // launch that writes each step to its own buffer of a ring); the pull's es does the same for the
-// source.
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+// source.  With DEFER, f* is written to res[0..Q) instead of being stored (the caller stores it).
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, bool DEFER = false>
 __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>& a, typename Store<ST>::R (&f)[L::Q],
-                                          int node, long long ds = 0) {
+                                          int node, long long ds = 0, typename Store<ST>::R* res = nullptr) {
     using RS = typename Store<ST>::R;
     using R = RS;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
@@ -1355,9 +1362,13 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
         }
     }
 
-    sfor<Q>([&](auto i) {
-        Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + ds + node, f[i] - out[i]);
-    });
+    if constexpr (DEFER) {
+        sfor<Q>([&](auto i) { res[i] = f[i] - out[i]; });
+    } else {
+        sfor<Q>([&](auto i) {
+            Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + ds + node, f[i] - out[i]);
+        });
+    }
     return;
 
 readout:
@@ -1388,7 +1399,9 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs<typename Store<ST>:
     step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, (z * a.ny + y) * a.nx + x);
 }
 
-// The collisions of the two nodes of a shared pull (node, node + 1), one after the other.
+// The collisions of the two nodes of a shared pull (node, node + 1), one after the other, each
+// node stored on its own (the multi-step pair kernel: holding the first node's results as
+// step_two_joint does spilled there and measured 2-7% slower).
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
 __device__ __forceinline__ void step_two(const StepArgs<typename Store<ST>::R>& a, const F2 (&f2)[L::Q], int node) {
     float f[L::Q];
@@ -1398,10 +1411,27 @@ __device__ __forceinline__ void step_two(const StepArgs<typename Store<ST>::R>& 
     step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
 }
 
+// The same two collisions with one 32-bit store per population holding both nodes' f* (node is
+// even, so the pair is 4-byte aligned): the first node's Q results stay live in FP32 across the
+// second collision, and each pair is rounded exactly as the per-node stores round.
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
+__device__ __forceinline__ void step_two_joint(const StepArgs<typename Store<ST>::R>& a, const F2 (&f2)[L::Q],
+                                               int node) {
+    float f[L::Q], r0[L::Q], r1[L::Q];
+    sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
+    step_body<L, ST, CLOSURE, FORMULA, FORCE, true>(a, f, node, 0, r0);
+    sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
+    step_body<L, ST, CLOSURE, FORMULA, FORCE, true>(a, f, node + 1, 0, r1);
+    if (a.readout) return;  // the read-out stored S, tau, drho and u itself
+    sfor<L::Q>([&](auto i) { Store<ST>::st2(static_cast<ST*>(a.dstp[CV(i)]) + node, r0[i], r1[i]); });
+}
+
 // Two x-adjacent nodes per thread that share the pull (paired loads where c_x = 0, adjacent
-// scalar loads otherwise) and then collide one after the other in scalar arithmetic.  Bound to 7
-// resident blocks per SM (72 registers; a few spilled values): measured faster than the 80
-// registers and 6 blocks it takes unbounded, and than 64 registers with more spills.
+// scalar loads otherwise), collide one after the other in scalar arithmetic and store both nodes
+// with one paired store per population (measured on a 512^3 FP16 box: Yu +10%, Chai +4% with the
+// Smagorinsky closure, +20% with a fixed tau, against per-node stores).  Bound to 7 resident
+// blocks per SM (72 registers; a few spilled values): measured faster than the 80 registers and 6
+// blocks it takes unbounded, and than 64 registers with more spills.
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
 __global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typename Store<ST>::R> a) {
     pdl_wait();
@@ -1413,7 +1443,7 @@ __global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typenam
     F2 f2[L::Q];
     pull2<L, ST>(a, x, y, z, f2);
     const int node = (z * a.ny + y) * a.nx + x;
-    step_two<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, node);
+    step_two_joint<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, node);
 }
 
 // ------------------------------------------------------------------------------------------
