@@ -91,44 +91,58 @@ __device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R
 
 // The scheduler: takes tickets until the launch's steps are exhausted and calls run(k, z, y0, y1)
 // for step k (0-based within the launch) of unit (z, band) once its neighbours have finished step
-// k - 1.  Every thread of the block calls it; run must not synchronise the block.
+// k - 1.  Every thread of the block calls it; run must not synchronise the block.  Two barriers
+// per unit: after the dependency waits, and after the unit's work, before which thread 0 (its own
+// share done) already takes the next ticket.  Everything the scheduler needs after the unit's
+// work is in shared memory or recomputed from the launch's constants, so none of its values stays
+// live in registers across the work (measured on the channel: FP32 Yu +1.4%, FP32 Chai +0.7%,
+// FP16 Chai +1.7%, FP16 Yu -1.7%, against three barriers per unit and the values kept live).
 template <class Run>
 __device__ __forceinline__ void stream_schedule(int ny, int nz, const StreamCtl& c, Run&& run) {
-    __shared__ int s_ticket, s_skip;
-    int* const err = c.sync;
-    int* const ticket = c.sync + 1;
-    int* const done = c.sync + 2;
-    const int tiles = c.tiles_y, units = nz * tiles;
-    const int total = c.steps * units;  // the host keeps it below 2^31
+    __shared__ int s_ticket, s_skip, s_unit, s_kp1;
+    // c.sync[0]: the error flag; c.sync[1]: the ticket counter; c.sync[2 + unit]: the units' step counts
+    if (threadIdx.x == 0) s_ticket = atomicAdd(c.sync + 1, 1) + c.first_step * nz * c.tiles_y;
+    __syncthreads();
     for (;;) {
-        // (the previous unit's last barrier orders these writes after every read of them)
-        if (threadIdx.x == 0) {
-            s_ticket = atomicAdd(ticket, 1) + c.first_step * units;
-            s_skip = 0;
-        }
-        __syncthreads();
-        const int t = s_ticket;
-        if (t >= total) return;
-        const int k = t / units, p = t - k * units;
-        const int pz = p / tiles, py = p - pz * tiles;
-        const int z = zigzag(pz, nz), ty = zigzag(py, tiles);
-        if (threadIdx.x < 9) {
-            bool ok = true;
-            if (k > 0) {
-                int zz = z + (int)threadIdx.x / 3 - 1, yy = ty + (int)threadIdx.x % 3 - 1;
-                zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-                yy = yy < 0 ? yy + tiles : (yy >= tiles ? yy - tiles : yy);
-                ok = wait_count(done + zz * tiles + yy, k, err);
+        int k, z, ty;
+        {
+            const int tiles = c.tiles_y, units = nz * tiles;
+            const int t = s_ticket;
+            if (t >= c.steps * units) return;  // the host keeps steps * units below 2^31
+            k = t / units;
+            const int p = t - k * units;
+            const int pz = p / tiles, py = p - pz * tiles;
+            z = zigzag(pz, nz);
+            ty = zigzag(py, tiles);
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                bool ok = true;
+                if (lane < 9) {
+                    if (k > 0) {
+                        int zz = z + lane / 3 - 1, yy = ty + lane % 3 - 1;
+                        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+                        yy = yy < 0 ? yy + tiles : (yy >= tiles ? yy - tiles : yy);
+                        ok = wait_count(c.sync + 2 + zz * tiles + yy, k, c.sync);
+                    }
+                    if (ok && ld_acquire(c.sync) != 0) ok = false;
+                }
+                const bool bad = __any_sync(0xffffffffu, !ok);
+                if (lane == 0) {
+                    s_skip = bad ? 1 : 0;
+                    s_unit = z * tiles + ty;
+                    s_kp1 = k + 1;
+                }
             }
-            if (!ok || ld_acquire(err) != 0) s_skip = 1;
         }
         __syncthreads();
         if (!s_skip) {
             const int y0 = ty * c.rows, y1 = min(ny, y0 + c.rows);
             run(k, z, y0, y1);
         }
+        // every thread read s_ticket before the barrier above, so thread 0 may replace it now
+        if (threadIdx.x == 0) s_ticket = atomicAdd(c.sync + 1, 1) + c.first_step * nz * c.tiles_y;
         __syncthreads();
-        if (threadIdx.x == 0) st_release(done + z * tiles + ty, k + 1);
+        if (threadIdx.x == 0) st_release(c.sync + 2 + s_unit, s_kp1);
     }
 }
 
