@@ -10,8 +10,10 @@
 // unit pulls were written by them in the previous step (read after write), and the buffer the
 // unit writes was last read by them in the previous step (write after read).
 //
-// Forward progress: a block holds a ticket only while it is resident, and every dependency of a
-// ticket is an earlier ticket, so the earliest unfinished ticket can always run.  Units are
+// Forward progress: a block holds a ticket only while it is resident, every dependency of a
+// ticket is an earlier ticket, and a block that takes its next ticket before publishing its
+// current unit publishes it without waiting on any other block; so the earliest unfinished
+// ticket can always run.  Units are
 // visited in a zigzag order (0, n-1, 1, n-2, ...) along z and along the y tiles, so the first
 // units of a step depend only on the first units of the previous step and the steps overlap
 // without stalls once there are more units than resident blocks.
