@@ -342,12 +342,29 @@ def run_ours(args):
 
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    lat = make_lattice(args.precision, args.formula, lattice=args.lattice, closure=args.closure)
+    if args.workload == "cavity":
+        lat = cavity_lattice(4096, args.n_index, args.formula)
+        lname, bytes_per_lup, grid, force = "D2Q9", 72, [4096, 4096, 1], "noforce"
+        workload = ("D2Q9 MRT power-law lid-driven cavity 4096x4096, n=%g, lid velocity %g, Re=%g, fluid at rest "
+                    "at t=0" % (args.n_index, CAVITY_U, CAVITY_RE))
+        closure, cl_tag, l2 = "power law, n=%g" % args.n_index, "POWERLAW", "two 604 MB population buffers"
+    elif args.workload == "box":
+        n = args.box_n
+        lat = box_lattice(n, args.precision, args.formula, 8, 0.03, 4)
+        lname, bytes_per_lup, grid, force = "D3Q19", BYTES_PER_LUP[args.precision], [n, n, n], "noforce"
+        workload = ("D3Q19 MRT Smagorinsky periodic box %d^3, divergence-free random Fourier start |k|<=8, "
+                    "rms 0.03, Cs=%g, tau0=%g" % (n, CS, TAU0))
+        closure, cl_tag = CLOSURE_NOTE["smag"], "SMAG"
+        l2 = "two %.0f MB population buffers" % (n ** 3 * bytes_per_lup / 2 / 1e6)
+    else:
+        lat = make_lattice(args.precision, args.formula, lattice=args.lattice, closure=args.closure)
+        lname = "D3Q%d" % args.lattice
+        bytes_per_lup = BYTES_PER_LUP[args.precision] * args.lattice // 19
+        if args.closure == "smag_lagged":  # the stored tau, read and written
+            bytes_per_lup += 16 if args.precision == "fp64" else 8
+        grid, force, workload = [NX, NY, NZ], "force", WORKLOAD.replace("D3Q19", lname)
+        closure, cl_tag, l2 = CLOSURE_NOTE[args.closure], args.closure.upper(), "two 319 MB population buffers"
     N = lat.N
-    lname = "D3Q%d" % args.lattice
-    bytes_per_lup = BYTES_PER_LUP[args.precision] * args.lattice // 19
-    if args.closure == "smag_lagged":  # the stored tau, read and written
-        bytes_per_lup += 16 if args.precision == "fp64" else 8
 
     # timed region: barrier + synchronize on both sides, max over ranks
     lat.step(args.warmup)
@@ -375,17 +392,20 @@ def run_ours(args):
     k_iso = statistics.mean(time_steps(lat, min(args.steps, 500), 0, per_launch=True))
 
     streamed = launches < args.steps
-    kernel = "%s<%s,%s,%s,%s,force>" % ("k_step_stream" if streamed else "k_step", lname, args.precision,
-                                         args.closure.upper(), args.formula.upper())
+    pair = args.precision in ("fp16s", "bf16s") and grid[0] % 2 == 0
+    kname = ("k_step_stream_pair" if pair else "k_step_stream") if streamed else ("k_step_pair_seq" if pair else "k_step")
+    kernel = "%s<%s,%s,%s,%s,%s>" % (kname, lname, args.precision, cl_tag, args.formula.upper(), force)
     out = {
-        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "channel" else METRIC.replace(
+            "Smagorinsky LES channel", "power-law cavity" if args.workload == "cavity" else "Smagorinsky box"),
+        "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("D3Q19", lname), "lattice": lname, "grid": [NX, NY, NZ],
-                   "formula": args.formula, "closure": CLOSURE_NOTE[args.closure],
+        "config": {"workload": workload, "lattice": lname, "grid": grid,
+                   "formula": args.formula, "closure": closure,
                    "precision": STORAGE_NOTE[args.precision],
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (two 319 MB population buffers per step)"},
+                   "l2": "inputs larger than L2 (%s per step)" % l2},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4),
                      "traffic": captured_traffic(kernel),
@@ -396,7 +416,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-    if rank == 0 and args.quick:
+    if rank == 0 and (args.quick or args.workload != "channel"):
         print(json.dumps(out), flush=True)
     elif rank == 0:
         # end to end through the C ABI with host buffers
@@ -855,11 +875,18 @@ def main():
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
                     help="replicas: one channel per rank (default, weak scaling); slab: one channel cut into "
                          "z-slabs over the ranks, halos exchanged every step (strong scaling)")
+    ap.add_argument("--workload", default="channel", choices=["channel", "cavity", "box"],
+                    help="channel: the headline (default); cavity: the D2Q9 power-law 4096^2 cavity (FP32); box: "
+                         "the periodic Smagorinsky box (--box-n); the last two print the timed line only")
+    ap.add_argument("--n-index", type=float, default=0.5, help="the cavity's power-law index n")
+    ap.add_argument("--box-n", type=int, default=512, help="the box's side")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--quick", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "cavity" and args.precision != "fp32":
+        ap.error("the cavity runs FP32 populations")
     if args.impl == "reference":
         run_reference(args)
     elif args.decomp == "slab":
