@@ -162,12 +162,16 @@ __device__ __forceinline__ void stream_steps(const StepArgs<typename Store<ST>::
     });
 }
 
-// One node per thread, 8 resident blocks (64 registers) for the Yu route and for Chai with the
-// Smagorinsky and power-law closures (Chai: 24 B of spills, measured 4.5% faster than 7 blocks at
-// 72 registers on the channel), 7 for the other Chai forms (spills of 64-144 B at 64 registers).
-// Unbounded, the unit loop costs 7-8 more registers and a block.
+// One node per thread.  9 resident blocks (56 registers, a few spilled values) for the Yu route
+// with the Smagorinsky closure: against 8 blocks at 64 registers, D3Q15 channel +4%, 128^3 box
+// +1%, the adjoint's forward sweep +4%, the D3Q19 channel unchanged (A/B on one box).  8 blocks
+// (64 registers) for the other Yu forms and for Chai with the Smagorinsky and power-law closures
+// (Chai: measured 4.5% faster than 7 blocks at 72 registers on the channel, 1.8% faster than 9
+// blocks at 56), 7 for the other Chai forms (spills of 64-144 B at 64 registers).  Unbounded, the
+// unit loop costs 7-8 more registers and a block.
 template <int CLOSURE, int FORMULA>
 constexpr int stream_min_blocks() {
+    if (FORMULA == F_YU && CLOSURE == CL_SMAG) return 9;
     return (FORMULA == F_YU || CLOSURE == CL_SMAG || CLOSURE == CL_POWERLAW) ? 8 : 7;
 }
 
