@@ -191,9 +191,10 @@ __global__ void __launch_bounds__(128, 7) k_step_stream_pair(const StepArgs<type
     stream_steps<L, ST, CLOSURE, FORMULA, FORCE, true>(a0, a1, c);
 }
 
-// Ring launch (see stream_steps), one node per thread.
+// Ring launch (see stream_steps), one node per thread; 9 resident blocks for the Yu route (the
+// adjoint's recompute: its whole call 0.7% shorter than with 8).
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128, FORMULA == F_YU ? 8 : 7)
+__global__ void __launch_bounds__(128, FORMULA == F_YU ? 9 : 7)
     k_step_stream_ring(const StepArgs<typename Store<ST>::R> a, const StreamCtl c) {
     stream_schedule(a.ny, a.nz, c, [&](int k, int z, int y0, int y1) {
         const long long sh = k * c.ring;
