@@ -164,19 +164,20 @@ __device__ __forceinline__ void stream_steps(const StepArgs<typename Store<ST>::
 
 // One node per thread.  9 resident blocks (56 registers, a few spilled values) for the Yu route
 // with the Smagorinsky closure: against 8 blocks at 64 registers, D3Q15 channel +4%, 128^3 box
-// +1%, the adjoint's forward sweep +4%, the D3Q19 channel unchanged (A/B on one box).  8 blocks
-// (64 registers) for the other Yu forms and for Chai with the Smagorinsky and power-law closures
-// (Chai: measured 4.5% faster than 7 blocks at 72 registers on the channel, 1.8% faster than 9
-// blocks at 56), 7 for the other Chai forms (spills of 64-144 B at 64 registers).  Unbounded, the
-// unit loop costs 7-8 more registers and a block.
-template <int CLOSURE, int FORMULA>
+// +1%, the adjoint's forward sweep +4%, the D3Q19 channel unchanged (A/B on one box; 10 blocks on
+// D3Q15 -1%).  9 blocks for D3Q15 Chai with the Smagorinsky closure too (56 registers, no spills:
+// +4.6%).  8 blocks (64 registers) for the other Yu forms and for D3Q19 Chai with the Smagorinsky
+// and power-law closures (Chai: measured 4.5% faster than 7 blocks at 72 registers on the channel,
+// 1.8% faster than 9 blocks at 56), 7 for the other Chai forms (spills of 64-144 B at 64
+// registers).  Unbounded, the unit loop costs 7-8 more registers and a block.
+template <int CLOSURE, int FORMULA, int Q>
 constexpr int stream_min_blocks() {
-    if (FORMULA == F_YU && CLOSURE == CL_SMAG) return 9;
+    if (CLOSURE == CL_SMAG && (FORMULA == F_YU || Q == 15)) return 9;
     return (FORMULA == F_YU || CLOSURE == CL_SMAG || CLOSURE == CL_POWERLAW) ? 8 : 7;
 }
 
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128, stream_min_blocks<CLOSURE, FORMULA>())
+__global__ void __launch_bounds__(128, stream_min_blocks<CLOSURE, FORMULA, L::Q>())
     k_step_stream(const StepArgs<typename Store<ST>::R> a0, const StepArgs<typename Store<ST>::R> a1,
                   const StreamCtl c) {
     stream_steps<L, ST, CLOSURE, FORMULA, FORCE, false>(a0, a1, c);
