@@ -51,3 +51,13 @@ def test_reference_arm_does_nothing_off_rank_zero(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_bench_rejects_a_16bit_cavity():
+    """The power-law cavity workload is FP32 only: the command line says so before any GPU work."""
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), "--workload",
+                        "cavity", "--precision", "fp16s"], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2 and "FP32" in r.stderr
