@@ -363,7 +363,8 @@ def run_ours(args):
         if args.closure == "smag_lagged":  # the stored tau, read and written
             bytes_per_lup += 16 if args.precision == "fp64" else 8
         grid, force, workload = [NX, NY, NZ], "force", WORKLOAD.replace("D3Q19", lname)
-        closure, cl_tag, l2 = CLOSURE_NOTE[args.closure], args.closure.upper(), "two 319 MB population buffers"
+        closure, cl_tag = CLOSURE_NOTE[args.closure], args.closure.upper()
+        l2 = "two %.0f MB population buffers" % (NX * NY * NZ * BYTES_PER_LUP[args.precision] * args.lattice // 19 / 2 / 1e6)
     N = lat.N
 
     # timed region: barrier + synchronize on both sides, max over ranks
@@ -501,7 +502,8 @@ def run_slab(args):
            "config": {"workload": WORKLOAD, "lattice": "D3Q19", "grid": [NX, NY, NZ], "formula": args.formula,
                       "closure": CLOSURE_NOTE["smag"], "precision": STORAGE_NOTE[args.precision],
                       "parallelism": "z-slabs over %d rank(s), halos exchanged every step" % world,
-                      "l2": "inputs larger than L2 (two 319 MB population buffers per step, split over the ranks)"},
+                      "l2": "inputs larger than L2 (two %.0f MB population buffers per step, split over the ranks)"
+                            % (NX * NY * NZ * bpl / 2 / 1e6)},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                         "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
                         "kernel": "k_step<D3Q19,%s,SMAG,%s,force> + halo copies + exchange" % (args.precision,

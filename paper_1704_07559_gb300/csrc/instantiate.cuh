@@ -4,13 +4,16 @@
 
 #include "launch.h"
 #include "step.cuh"
+#include "step_pair.cuh"
 
 namespace lbm {
 
 // Step kernel selection: one node per thread (k_step), except 16-bit storage with nx even and no
-// read-out, which runs two x-adjacent nodes per thread sharing the pull (k_step_pair_seq; the
-// 16-bit step is issue-bound and the shared pull saves instructions; FP32 and FP64 measured
-// slower in that form and stay one node per thread).
+// read-out, which runs two x-adjacent nodes per thread in packed FP32-pair arithmetic
+// (k_step_pair_seq, step_pair.cuh: the 16-bit step is issue-bound, and the shared pull and the
+// pair instructions halve its arithmetic per node).  FP32 storage stays one node per thread: its
+// step already runs at the HBM bound, and it keeps the delta form, whose FP32 rounding acts on
+// the collision increment only; FP64 is bound by its arithmetic.
 template <class L, class ST, int C, int F, bool FO>
 cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
     if constexpr (sizeof(ST) == 2) {

@@ -17,8 +17,9 @@
 // With a closure the viscous rates are unknown, so both routes split S = A + s_nu B (exact:
 // S is linear in the rates) and solve the scalar fixed point for tau = 1/s_nu.
 //
-// A thread owns one node, or (16-bit storage) two x-adjacent nodes that share the pull's address
-// arithmetic and then collide one after the other.
+// A thread owns one node (this file), or with 16-bit storage two x-adjacent nodes that share the
+// pull's address arithmetic and collide side by side in packed FP32-pair arithmetic
+// (step_pair.cuh, which forms f* from the post-collision moments instead of in delta form).
 //
 // All lattice coefficients enter as compile-time constants: loops over populations and moments
 // are compile-time sequences (sfor) so each entry of T and c folds into an add, a subtract or
@@ -58,7 +59,7 @@ __host__ __device__ __forceinline__ void sfor(F&& f) {
 __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 
-// the populations of two x-adjacent nodes (a plain pair: the arithmetic is scalar)
+// the pulled populations of two x-adjacent nodes (lo: the even node, hi: the odd one)
 struct F2 {
     float2 v;
     F2() = default;
@@ -303,6 +304,10 @@ template <class L>
 __host__ __device__ constexpr uint32_t mask_all_but_density() {
     return ((1u << L::Q) - 1u) & ~1u;
 }
+template <class L>
+__host__ __device__ constexpr uint32_t mask_all() {
+    return (1u << L::Q) - 1u;
+}
 
 // Forward and backward transforms.  The generic form (any lattice) sums the nonzero entries of
 // each row of T over the opposite-pair sums and differences.  D3Q19 and D3Q15 have hand-factored forms
@@ -416,13 +421,13 @@ struct Xf<D3Q19> {
     template <uint32_t USE, class R>
     static __device__ __forceinline__ void backward(const R (&a)[19], R (&out)[19]) {
         constexpr uint32_t NC = mask_nonconserved<D3Q19>();
-        if constexpr (USE != NC && USE != mask_all_but_density<D3Q19>()) {
+        if constexpr (USE != NC && USE != mask_all_but_density<D3Q19>() && USE != mask_all<D3Q19>()) {
             back_transform<D3Q19, USE>(a, out);
         } else {
-            constexpr bool CONS = (USE >> 3) & 1u;
-            out[0] = fma(R(12.0f), a[2], R(-30.0f) * a[1]);
+            constexpr bool CONS = (USE >> 3) & 1u, DENS = USE & 1u;  // T_0i = 1 for every i
+            out[0] = DENS ? fma(R(12.0f), a[2], fma(R(-30.0f), a[1], a[0])) : fma(R(12.0f), a[2], R(-30.0f) * a[1]);
             // axis populations
-            const R B1 = fma(R(-4.0f), a[2], R(-11.0f) * a[1]);
+            const R B1 = DENS ? fma(R(-4.0f), a[2], fma(R(-11.0f), a[1], a[0])) : fma(R(-4.0f), a[2], R(-11.0f) * a[1]);
             const R C = fma(R(2.0f), a[10], -a[9]);
             const R W = fma(R(-2.0f), a[12], a[11]);
             const R Ex = fma(R(-2.0f), C, B1);
@@ -446,7 +451,7 @@ struct Xf<D3Q19> {
             out[5] = Ez + Oz;
             out[6] = Ez - Oz;
             // edge populations
-            const R B2 = fma(R(8.0f), a[1], a[2]);
+            const R B2 = DENS ? fma(R(8.0f), a[1], a[2] + a[0]) : fma(R(8.0f), a[1], a[2]);
             const R G = a[9] + a[10], H = a[11] + a[12];
             R X = a[4], Y = a[6], Z = a[8];
             if constexpr (CONS) {
@@ -556,13 +561,13 @@ struct Xf<D3Q15> {
     template <uint32_t USE, class R>
     static __device__ __forceinline__ void backward(const R (&a)[15], R (&out)[15]) {
         constexpr uint32_t NC = mask_nonconserved<D3Q15>();
-        if constexpr (USE != NC && USE != mask_all_but_density<D3Q15>()) {
+        if constexpr (USE != NC && USE != mask_all_but_density<D3Q15>() && USE != mask_all<D3Q15>()) {
             back_transform<D3Q15, USE>(a, out);
         } else {
-            constexpr bool CONS = (USE >> 3) & 1u;
-            out[0] = fma(R(16.0f), a[2], R(-2.0f) * a[1]);
+            constexpr bool CONS = (USE >> 3) & 1u, DENS = USE & 1u;  // T_0i = 1 for every i
+            out[0] = DENS ? fma(R(16.0f), a[2], fma(R(-2.0f), a[1], a[0])) : fma(R(16.0f), a[2], R(-2.0f) * a[1]);
             // axis populations
-            const R B1 = fma(R(-4.0f), a[2], -a[1]);
+            const R B1 = DENS ? fma(R(-4.0f), a[2], a[0] - a[1]) : fma(R(-4.0f), a[2], -a[1]);
             const R Ex = fma(R(2.0f), a[9], B1), BC = B1 - a[9];
             const R Ey = BC + a[10], Ez = BC - a[10];
             R Ox, Oy, Oz, X = a[4], Y = a[6], Z = a[8];
@@ -585,7 +590,7 @@ struct Xf<D3Q15> {
             out[5] = Ez + Oz;
             out[6] = Ez - Oz;
             // corner populations: even parts B2 +- a11 +- a12 +- a13, odd parts +-X +-Y +-Z +- a14
-            const R B2 = a[1] + a[2];
+            const R B2 = DENS ? (a[1] + a[2]) + a[0] : a[1] + a[2];
             const R s = B2 + a[11], t = B2 - a[11], g = a[12] + a[13], h = a[12] - a[13];
             const R U = Z + Y, V = Z - Y, p = X + a[14], r = a[14] - X;
             const R E3 = s + g, E6 = s - g, E4 = t + h, E5 = t - h;
@@ -1197,10 +1202,10 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 // by the chosen route, closure, relaxation, force, and either the store of f* or (readout) the
 // store of S, tau, drho and u.  ds shifts the populations' destination by that many elements (a
 // launch that writes each step to its own buffer of a ring); the pull's es does the same for the
-// source.  With DEFER, f* is written to res[0..Q) instead of being stored (the caller stores it).
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, bool DEFER = false>
+// source.
+template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
 __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>& a, typename Store<ST>::R (&f)[L::Q],
-                                          int node, long long ds = 0, typename Store<ST>::R* res = nullptr) {
+                                          int node, long long ds = 0) {
     using RS = typename Store<ST>::R;
     using R = RS;
     constexpr int Q = L::Q, NS = L::NS, NP = L::NP;
@@ -1367,13 +1372,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
         }
     }
 
-    if constexpr (DEFER) {
-        sfor<Q>([&](auto i) { res[i] = f[i] - out[i]; });
-    } else {
-        sfor<Q>([&](auto i) {
-            Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + ds + node, f[i] - out[i]);
-        });
-    }
+    sfor<Q>([&](auto i) { Store<ST>::st(static_cast<ST*>(a.dstp[CV(i)]) + ds + node, f[i] - out[i]); });
     return;
 
 readout:
@@ -1410,53 +1409,6 @@ __global__ void __launch_bounds__(128, step_min_blocks<L, ST>()) k_step(const St
     typename Store<ST>::R f[L::Q];
     pull<L, ST>(a, x, y, z, f);
     step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, (z * a.ny + y) * a.nx + x);
-}
-
-// The collisions of the two nodes of a shared pull (node, node + 1), one after the other, each
-// node stored on its own (the multi-step pair kernel: holding the first node's results as
-// step_two_joint does spilled there and measured 2-7% slower).
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__device__ __forceinline__ void step_two(const StepArgs<typename Store<ST>::R>& a, const F2 (&f2)[L::Q], int node) {
-    float f[L::Q];
-    sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node);
-    sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE>(a, f, node + 1);
-}
-
-// The same two collisions with one 32-bit store per population holding both nodes' f* (node is
-// even, so the pair is 4-byte aligned): the first node's Q results stay live in FP32 across the
-// second collision, and each pair is rounded exactly as the per-node stores round.
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__device__ __forceinline__ void step_two_joint(const StepArgs<typename Store<ST>::R>& a, const F2 (&f2)[L::Q],
-                                               int node) {
-    float f[L::Q], r0[L::Q], r1[L::Q];
-    sfor<L::Q>([&](auto i) { f[i] = f2[i].lo(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE, true>(a, f, node, 0, r0);
-    sfor<L::Q>([&](auto i) { f[i] = f2[i].hi(); });
-    step_body<L, ST, CLOSURE, FORMULA, FORCE, true>(a, f, node + 1, 0, r1);
-    if (a.readout) return;  // the read-out stored S, tau, drho and u itself
-    sfor<L::Q>([&](auto i) { Store<ST>::st2(static_cast<ST*>(a.dstp[CV(i)]) + node, r0[i], r1[i]); });
-}
-
-// Two x-adjacent nodes per thread that share the pull (paired loads where c_x = 0, adjacent
-// scalar loads otherwise), collide one after the other in scalar arithmetic and store both nodes
-// with one paired store per population (measured on a 512^3 FP16 box: Yu +10%, Chai +4% with the
-// Smagorinsky closure, +20% with a fixed tau, against per-node stores).  Bound to 7 resident
-// blocks per SM (72 registers; a few spilled values): measured faster than the 80 registers and 6
-// blocks it takes unbounded, and than 64 registers with more spills.
-template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128, 7) k_step_pair_seq(const StepArgs<typename Store<ST>::R> a) {
-    pdl_wait();
-    pdl_release();
-    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z + a.z0;
-    if (x >= a.nx || y >= a.ny) return;
-    F2 f2[L::Q];
-    pull2<L, ST>(a, x, y, z, f2);
-    const int node = (z * a.ny + y) * a.nx + x;
-    step_two_joint<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, node);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -28,6 +28,7 @@
 
 #include "launch.h"
 #include "step.cuh"
+#include "step_pair.cuh"
 
 namespace lbm {
 
@@ -68,7 +69,7 @@ __device__ __noinline__ static bool wait_count(const int* flag, int want, int* e
 }
 
 // One unit: rows [y0, y1) of plane z, one node per thread (PAIR false) or two x-adjacent nodes
-// per thread sharing the pull (PAIR true, nx even).  es / ds shift the source / destination
+// per thread in packed pair arithmetic (PAIR true, nx even).  es / ds shift the source / destination
 // populations by that many elements (ring launches; one node per thread only).
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE, bool PAIR>
 __device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R>& a, int z, int y0, int y1,
@@ -79,7 +80,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs<typename Store<ST>::R
             for (int x = 2 * (int)threadIdx.x; x < a.nx; x += 2 * (int)blockDim.x) {
                 F2 f2[L::Q];
                 pull2<L, ST, true>(a, x, y, z, f2);
-                step_two<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, (z * a.ny + y) * a.nx + x);
+                step_pair<L, ST, CLOSURE, FORMULA, FORCE>(a, f2, (z * a.ny + y) * a.nx + x);
             }
         } else {
             for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
@@ -183,10 +184,10 @@ __global__ void __launch_bounds__(128, stream_min_blocks<CLOSURE, FORMULA, L::Q>
     stream_steps<L, ST, CLOSURE, FORMULA, FORCE, false>(a0, a1, c);
 }
 
-// Two nodes per thread sharing the pull (16-bit storage, nx even): 7 resident blocks, as the
-// one-step pair kernel.
+// Two nodes per thread in packed pair arithmetic (16-bit storage, nx even; step_pair.cuh): 7
+// resident blocks, as the one-step pair kernel.
 template <class L, class ST, int CLOSURE, int FORMULA, bool FORCE>
-__global__ void __launch_bounds__(128, 7) k_step_stream_pair(const StepArgs<typename Store<ST>::R> a0,
+__global__ void __launch_bounds__(128, PAIR_MIN_BLOCKS) k_step_stream_pair(const StepArgs<typename Store<ST>::R> a0,
                                                              const StepArgs<typename Store<ST>::R> a1,
                                                              const StreamCtl c) {
     stream_steps<L, ST, CLOSURE, FORMULA, FORCE, true>(a0, a1, c);

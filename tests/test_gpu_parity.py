@@ -159,6 +159,12 @@ CASES = [
     # even nx with walls at x: the two-node kernel's general pull at the x faces
     (19, (40, 8, 6), "fp16s", "smag", "yu", dict(tau=0.51, bc=["wall"] * 2 + ["periodic"] * 2 + ["wall", "lid"],
                                                   lid={5: (0.04, 0.0, 0.0)})),
+    # even nx, the two-node kernel's packed pair arithmetic with the per-node force field (read as
+    # one pair per component), on both routes, and with fixed rates
+    (19, (34, 17, 5), "fp16s", "smag", "chai", dict(tau=0.51, force_field=True)),
+    (19, (34, 17, 5), "bf16s", "smag", "yu", dict(tau=0.51, force_field=True)),
+    (19, (66, 7, 5), "bf16s", "newton", "yu", dict(force=[1e-5, -2e-5, 3e-6])),
+    (15, (34, 9, 6), "fp16s", "smag", "chai", dict(tau=0.51, force_field=True)),
     (9, (150, 37, 1), "fp64", "powerlaw", "chai", dict(bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)},
                                                        pl=(0.5, 7e-4), tau=1.0)),
     (9, (150, 37, 1), "fp32", "powerlaw", "chai", dict(bc=["wall"] * 3 + ["lid"], lid={3: (0.05, 0.0, 0.0)},
