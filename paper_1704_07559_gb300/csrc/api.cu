@@ -469,11 +469,49 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
             return lbm::adj_fold_f32(acc, dLdg, c->p.rho0, 3LL * c->N, s);
     };
 
+    const long long ring = (long long)(L.state / c->elem_bytes);  // elements between segment states
+    const int forced = c->schedule == LBM_SCHEDULE_STREAM ? 1 : 0;
+    // states 1 .. m - 1 of segment sgi into the segment buffers sg(0 .. m - 2), from its checkpoint:
+    // the first step from the checkpoint, the rest (FP32, where the schedule allows) in one ring
+    // launch that writes each step to the next state buffer
+    auto fill_segment = [&](int sgi, int m) -> cudaError_t {
+        cudaError_t err;
+        int i = 1;
+        if (m >= 2) {
+            err = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, cp(sgi), sg(0));
+            if (err != cudaSuccess) return err;
+            i = 2;
+        }
+        if constexpr (!F64) {
+            if (m - 2 >= 2 && c->schedule != LBM_SCHEDULE_PER_STEP) {
+                lbm::StepArgs<float> ra;
+                fill_args(c, &ra);
+                ra.readout = 0;
+                ra.S_out = ra.tau_out = ra.drho_out = ra.u_out = nullptr;
+                set_buffers(c, &ra, sg(0), sg(1));
+                const lbm::StreamCtl ctl = {c->sync, m - 2, c->stream_rows, c->stream_tiles, 0, ring};
+                err = lbm::stream_ring_d3q19_f32(ra, ctl, c->p.closure, c->p.formula, has_force(c) ? 1 : 0, forced, s);
+                if (err == cudaSuccess)
+                    i = m;
+                else if (err != cudaErrorNotSupported)
+                    return err;
+            }
+        }
+        for (; i < m; ++i) {
+            err = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, sg(i - 2), sg(i - 1));
+            if (err != cudaSuccess) return err;
+        }
+        return cudaSuccess;
+    };
+
     // forward T steps from the current state, keeping every seg-th state: per segment, the first
     // step reads the checkpoint into a context buffer, the middle steps ping-pong between the two
     // context buffers (several per launch where the schedule allows), and the last step writes the
-    // next checkpoint (the last segment ends in a context buffer)
+    // next checkpoint.  The last segment writes its states straight into the segment buffers the
+    // reverse sweep reads (so it needs no recomputation there) and its last step the final state
+    // into a context buffer.
     const void* fcur = c->buf[c->cur];
+    bool last_filled = false;
     if (T > 0) {
         e = cudaMemcpyAsync(cp(0), c->buf[c->cur], state_bytes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
@@ -483,6 +521,15 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
             if (to_cp && k1 - k0 == 1) {  // one-step segments: checkpoint to checkpoint
                 e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, cp(k0 / seg), cp(k1 / seg));
                 if (e != cudaSuccess) return e;
+                continue;
+            }
+            if (!to_cp && k1 - k0 >= 2) {  // the last segment
+                e = fill_segment(k0 / seg, k1 - k0);
+                if (e != cudaSuccess) return e;
+                e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, sg(k1 - k0 - 2), c->buf[0]);
+                if (e != cudaSuccess) return e;
+                c->cur = 0;
+                last_filled = true;
                 continue;
             }
             e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, cp(k0 / seg), c->buf[0]);
@@ -518,40 +565,17 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
     e = cudaMemsetAsync(dLdg, 0, sizeof(double) * 3 * c->N, s);
     if (e != cudaSuccess) return e;
 
-    // reverse sweep, segment by segment from the last, recomputing each segment's states
+    // reverse sweep, segment by segment from the last, recomputing the states of every segment but
+    // the last
     int lc = 0;
-    const long long ring = (long long)(L.state / c->elem_bytes);  // elements between segment states
-    const int forced = c->schedule == LBM_SCHEDULE_STREAM ? 1 : 0;
     for (int sgi = L.ncp - 1; sgi >= 0; --sgi) {
         const int k0 = sgi * seg, k1 = (k0 + seg < T) ? k0 + seg : T, m = k1 - k0;
         const void* states[1024];
         states[0] = cp(sgi);
         for (int i = 1; i < m; ++i) states[i] = sg(i - 1);
-        // recompute the segment's states: the first from the checkpoint, the rest (FP32, where the
-        // schedule allows) in one ring launch that writes each step to the next state buffer
-        int i = 1;
-        if (m >= 2) {
-            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, states[0], sg(0));
-            if (e != cudaSuccess) return e;
-            i = 2;
-        }
-        if constexpr (!F64) {
-            if (m - 2 >= 2 && c->schedule != LBM_SCHEDULE_PER_STEP) {
-                lbm::StepArgs<float> ra;
-                fill_args(c, &ra);
-                ra.readout = 0;
-                ra.S_out = ra.tau_out = ra.drho_out = ra.u_out = nullptr;
-                set_buffers(c, &ra, sg(0), sg(1));
-                const lbm::StreamCtl ctl = {c->sync, m - 2, c->stream_rows, c->stream_tiles, 0, ring};
-                e = lbm::stream_ring_d3q19_f32(ra, ctl, c->p.closure, c->p.formula, has_force(c) ? 1 : 0, forced, s);
-                if (e == cudaSuccess)
-                    i = m;
-                else if (e != cudaErrorNotSupported)
-                    return e;
-            }
-        }
-        for (; i < m; ++i) {
-            e = run_step(c, c->p.formula, 0, nullptr, nullptr, nullptr, nullptr, states[i - 1], sg(i - 1));
+        // recompute the segment's states (the last segment's are still there from the forward sweep)
+        if (!(sgi == L.ncp - 1 && last_filled)) {
+            e = fill_segment(sgi, m);
             if (e != cudaSuccess) return e;
         }
         // reverse steps k1 - 1 .. k0 + 1 (states sg(m - 2) down to sg(0), equally spaced) in one

@@ -960,19 +960,59 @@ __device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepAr
     return tau;
 }
 
-// A per-node field value loaded with an asm volatile ld (its issue point stays where it is written),
-// through L2: in a multi-step launch the value may have been written by another block
+// L2 eviction priority for per-node fields that every step reads again while the populations
+// stream past: the force field (read-only), the lagged closure's stored tau and the adjoint's
+// force-gradient accumulator (both read and rewritten by their own node each step).  Their loads and stores carry an evict_last policy, so
+// the field (12 B per node in FP32) can stay resident in L2 across the steps of a launch instead
+// of coming from HBM every step.  A hint only: the data are the same either way.
+__device__ __forceinline__ unsigned long long l2_keep() {
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// read-only field (non-coherent path), evict_last in L2
 template <class RS>
-__device__ __forceinline__ RS load_early(const RS* p) {
+__device__ __forceinline__ RS ld_keep(const RS* p) {
+    const unsigned long long pol = l2_keep();
     if constexpr (std::is_same<RS, double>::value) {
         double v;
-        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
         return v;
     } else {
         float v;
-        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
         return v;
     }
+}
+// an aligned FP32 pair (p 8-byte aligned) of a read-only field, evict_last in L2
+__device__ __forceinline__ float2 ld2_keep(const float* p) {
+    const unsigned long long pol = l2_keep();
+    float2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+// a field value written by another block earlier in the launch: loaded through L2 (asm volatile,
+// so its issue point stays where it is written) and stored back, both evict_last in L2
+template <class RS>
+__device__ __forceinline__ RS load_early_keep(const RS* p) {
+    const unsigned long long pol = l2_keep();
+    if constexpr (std::is_same<RS, double>::value) {
+        double v;
+        asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+        return v;
+    } else {
+        float v;
+        asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+        return v;
+    }
+}
+template <class RS>
+__device__ __forceinline__ void st_keep(RS* p, RS v) {
+    const unsigned long long pol = l2_keep();
+    if constexpr (std::is_same<RS, double>::value)
+        asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+    else
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
 }
 
 // Deviatoric Smagorinsky, tau = tau0 + 3 Cs^2 |S_d(1/tau)|.  On these bases the rate-free part A is
@@ -998,7 +1038,7 @@ __device__ __forceinline__ R solve_tau(const R (&A)[L::NS], const R (&B)[L::NS],
         const R tau = tau_prev;
         snu = c_rcp(tau);
         affine<L>(A, B, snu, S);
-        if (!a.readout) a.tau_field[node] = fma(a.smag_c3, c_sqrt(RS(2) * strain_dot<L>(S, S)), a.tau0);
+        if (!a.readout) st_keep(a.tau_field + node, RS(fma(a.smag_c3, c_sqrt(RS(2) * strain_dot<L>(S, S)), a.tau0)));
         return tau;
     } else if constexpr (CLOSURE == CL_SMAG_DEV) {
         const R tau = tau_deviatoric(strain_dot<L>(B, B), a);
@@ -1219,7 +1259,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     R F[3] = {R(0.0f), R(0.0f), R(0.0f)};
     if constexpr (FORCE) {
         if (a.force_field) {
-            sfor<L::D>([&](auto d) { F[d] = a.force_field[CV(d) * N + node]; });
+            sfor<L::D>([&](auto d) { F[d] = ld_keep(a.force_field + CV(d) * N + node); });
         } else {
             sfor<L::D>([&](auto d) { F[d] = R(a.F[d]); });
         }
@@ -1227,7 +1267,7 @@ __device__ __forceinline__ void step_body(const StepArgs<typename Store<ST>::R>&
     // the lagged closure's stored tau, loaded next to the populations so its latency overlaps theirs
     // (an asm volatile load keeps it there instead of next to its use after the moment arithmetic)
     R tau_prev = R(0.0f);
-    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_early(a.tau_field + node);
+    if constexpr (CLOSURE == CL_SMAG_LAGGED) tau_prev = load_early_keep(a.tau_field + node);
     const R ir0 = R(a.inv_rho0);
     R drho, j[3] = {R(0.0f), R(0.0f), R(0.0f)}, u[3] = {R(0.0f), R(0.0f), R(0.0f)};
     R S[NS], tau, snu;

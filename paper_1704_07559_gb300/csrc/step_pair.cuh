@@ -79,7 +79,7 @@ __device__ __forceinline__ void step_pair(const StepArgs<float>& a, const F2 (&f
     if constexpr (FORCE) {
         if (a.force_field) {
             sfor<L::D>([&](auto d) {
-                F[d] = V2(__ldg(reinterpret_cast<const float2*>(a.force_field + CV(d) * N + node)));
+                F[d] = V2(ld2_keep(a.force_field + CV(d) * N + node));
             });
         } else {
             sfor<L::D>([&](auto d) { F[d] = R(a.F[d]); });
