@@ -248,14 +248,14 @@ __global__ void __launch_bounds__(128) k_adjoint_step(const AdjArgs<typename Sto
     sfor<19>([&](auto i) { lam[i] = a.lamp_in[CV(i)][node]; });
     // the node's force-gradient accumulator, loaded with the other inputs (its latency overlaps
     // theirs instead of following the reverse map)
-    for (int d = 0; d < 3; ++d) acc[d] = load_early_keep(a.dF + d * N + node);
+    for (int d = 0; d < 3; ++d) acc[d] = load_early(a.dF + d * N + node);
     NodeFwd<R> st;
     node_forward<CLOSURE>(p, F, a.st, st);
     R mu[19], Fb[3];
     const R Sb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     node_backward<CLOSURE, true>(st, lam, Sb, R(0), a.st, mu, Fb);
     push(a, x, y, z, mu);
-    for (int d = 0; d < 3; ++d) st_keep(a.dF + d * N + node, acc[d] + Fb[d]);
+    for (int d = 0; d < 3; ++d) a.dF[d * N + node] = acc[d] + Fb[d];
 }
 
 // Several adjoint steps in one launch (the scheduler of step_stream.cuh): launch step k is the
@@ -280,14 +280,14 @@ __device__ __forceinline__ void adjoint_unit(const AdjArgs<typename Store<ST>::R
             sfor<19>([&](auto i) { lam[i] = __ldcg(a.lamp_in[CV(i)] + node); });
             // the accumulator (this node's own, last written by this unit's previous step, which
             // the unit's dependencies include) loaded with the other inputs
-            for (int d = 0; d < 3; ++d) acc[d] = load_early_keep(a.dF + d * N + node);
+            for (int d = 0; d < 3; ++d) acc[d] = load_early(a.dF + d * N + node);
             NodeFwd<R> st;
             node_forward<CLOSURE>(p, F, a.st, st);
             R mu[19], Fb[3];
             const R Sb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
             node_backward<CLOSURE, true>(st, lam, Sb, R(0), a.st, mu, Fb);
             push(a, x, y, z, mu);
-            for (int d = 0; d < 3; ++d) st_keep(a.dF + d * N + node, acc[d] + Fb[d]);
+            for (int d = 0; d < 3; ++d) a.dF[d * N + node] = acc[d] + Fb[d];
         }
     }
 }
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) k_functional(const AdjArgs<typename Store
         const R none[19] = {};
         node_backward<CLOSURE, false>(st, none, Sb, SS * cst<R>(1.0 / 3.0), a.st, mu, Fb);
         push(a, x, y, z, mu);
-        for (int d = 0; d < 3; ++d) st_keep(a.dF + d * N + node, Fb[d]);
+        for (int d = 0; d < 3; ++d) a.dF[d * N + node] = Fb[d];
     }
     // block sum of ell in FP64 (fixed order: warp tree, then warps in order)
     __shared__ double red[4];

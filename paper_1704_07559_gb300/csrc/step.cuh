@@ -961,10 +961,13 @@ __device__ __forceinline__ RS tau_fixed_point(RS qa, RS qb2, RS qc, const StepAr
 }
 
 // L2 eviction priority for per-node fields that every step reads again while the populations
-// stream past: the force field (read-only), the lagged closure's stored tau and the adjoint's
-// force-gradient accumulator (both read and rewritten by their own node each step).  Their loads and stores carry an evict_last policy, so
-// the field (12 B per node in FP32) can stay resident in L2 across the steps of a launch instead
-// of coming from HBM every step.  A hint only: the data are the same either way.
+// stream past: the force field (read-only) and the lagged closure's stored tau (read and rewritten
+// by its own node each step).  Their loads and stores carry an evict_last policy, so the field
+// (12 or 4 B per node in FP32) stays in L2 across the steps of a launch instead of coming from HBM
+// every step.  A hint only: the data are the same either way.  Measured on a GB300: one 25 MB
+// field stays (the same loads without the policy run at the old speed); two such fields hinted
+// at once in the adjoint's reverse step (force field and gradient accumulator) both kept
+// streaming from HBM, so only the force field carries the hint there.
 __device__ __forceinline__ unsigned long long l2_keep() {
     unsigned long long pol;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -1003,6 +1006,19 @@ __device__ __forceinline__ RS load_early_keep(const RS* p) {
     } else {
         float v;
         asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+        return v;
+    }
+}
+// the same load without the eviction policy
+template <class RS>
+__device__ __forceinline__ RS load_early(const RS* p) {
+    if constexpr (std::is_same<RS, double>::value) {
+        double v;
+        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    } else {
+        float v;
+        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return v;
     }
 }
