@@ -393,10 +393,7 @@ def run_ours(args):
     k_iso = statistics.mean(time_steps(lat, min(args.steps, 500), 0, per_launch=True))
 
     streamed = launches < args.steps
-    # two nodes per thread in pair arithmetic: 16-bit storage, and FP32 Chai on the 3D lattices with
-    # the Smagorinsky closure (nx even)
-    pair = grid[0] % 2 == 0 and (args.precision in ("fp16s", "bf16s") or (
-        args.precision == "fp32" and args.formula == "chai" and lname != "D2Q9" and cl_tag == "SMAG"))
+    pair = args.precision in ("fp16s", "bf16s") and grid[0] % 2 == 0
     kname = ("k_step_stream_pair" if pair else "k_step_stream") if streamed else ("k_step_pair_seq" if pair else "k_step")
     kernel = "%s<%s,%s,%s,%s,%s>" % (kname, lname, args.precision, cl_tag, args.formula.upper(), force)
     out = {

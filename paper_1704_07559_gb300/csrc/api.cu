@@ -482,13 +482,8 @@ cudaError_t adjoint_run(lbm_ctx* c, int T, int seg, char* work, const AdjLayout&
             if (err != cudaSuccess) return err;
             i = 2;
         }
-        // the ring launch runs one node per thread in delta form; where a step of this context runs
-        // two nodes per thread in pair arithmetic instead (FP32 Chai with nx even), the states are
-        // recomputed one launch per step so that they equal the forward sweep's bit for bit
-        const bool pair_steps = c->p.formula == LBM_CHAI && c->nx % 2 == 0 &&
-                                (c->p.closure == LBM_NEWTON || c->p.closure == LBM_SMAG);
         if constexpr (!F64) {
-            if (m - 2 >= 2 && c->schedule != LBM_SCHEDULE_PER_STEP && !pair_steps) {
+            if (m - 2 >= 2 && c->schedule != LBM_SCHEDULE_PER_STEP) {
                 lbm::StepArgs<float> ra;
                 fill_args(c, &ra);
                 ra.readout = 0;

@@ -8,14 +8,15 @@
 
 namespace lbm {
 
-// Step kernel selection: one node per thread (k_step), except where pair_form (step_pair.cuh)
-// says otherwise and the call, with nx even, is not a read-out: then two x-adjacent nodes per
-// thread in packed FP32-pair arithmetic (k_step_pair_seq: the shared pull and the pair
-// instructions halve the arithmetic per node of the steps that are bound by it, all 16-bit steps
-// and the FP32 Chai route).  FP64 is bound by its arithmetic and stays one node per thread.
+// Step kernel selection: one node per thread (k_step), except 16-bit storage with nx even and no
+// read-out, which runs two x-adjacent nodes per thread in packed FP32-pair arithmetic
+// (k_step_pair_seq, step_pair.cuh: the 16-bit step is issue-bound, and the shared pull and the
+// pair instructions halve its arithmetic per node).  FP32 storage stays one node per thread: its
+// step already runs at the HBM bound, and it keeps the delta form, whose FP32 rounding acts on
+// the collision increment only; FP64 is bound by its arithmetic.
 template <class L, class ST, int C, int F, bool FO>
 cudaError_t launch_form(const StepArgs<typename Store<ST>::R>& a, cudaStream_t s) {
-    if constexpr (pair_form<L, ST, C, F>()) {
+    if constexpr (sizeof(ST) == 2) {
         if (!a.readout && a.nx % 2 == 0) {
             dim3 g, b;
             lattice_grid(a.nx / 2, a.ny, a.nzc, &g, &b);

@@ -17,10 +17,9 @@
 // With a closure the viscous rates are unknown, so both routes split S = A + s_nu B (exact:
 // S is linear in the rates) and solve the scalar fixed point for tau = 1/s_nu.
 //
-// A thread owns one node (this file), or (16-bit storage; FP32 storage on the Chai route) two
-// x-adjacent nodes that share the pull's address arithmetic and collide side by side in packed
-// FP32-pair arithmetic (step_pair.cuh, which forms f* from the post-collision moments instead of
-// in delta form).
+// A thread owns one node (this file), or with 16-bit storage two x-adjacent nodes that share the
+// pull's address arithmetic and collide side by side in packed FP32-pair arithmetic
+// (step_pair.cuh, which forms f* from the post-collision moments instead of in delta form).
 //
 // All lattice coefficients enter as compile-time constants: loops over populations and moments
 // are compile-time sequences (sfor) so each entry of T and c folds into an add, a subtract or
@@ -117,9 +116,6 @@ struct Store<float> {
     static __device__ __forceinline__ R ldc(const float* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float* p, R v) { __stcs(p, v); }
     // aligned pair p[0], p[1] (p 8-byte aligned)
-    static __device__ __forceinline__ void st2(float* p, R lo, R hi) {
-        __stcs(reinterpret_cast<float2*>(p), make_float2(lo, hi));
-    }
     static __device__ __forceinline__ F2 ld2(const float* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
     static __device__ __forceinline__ F2 ld2c(const float* p) { return F2(__ldcg(reinterpret_cast<const float2*>(p))); }
 };

@@ -1,9 +1,8 @@
 // step_pair.cuh -- the step of two x-adjacent nodes per thread in packed FP32-pair arithmetic
-// (16-bit storage; FP32 storage on the Chai route).
+// (16-bit storage).
 //
 // The 16-bit step moves half the bytes of the FP32 step but executes the same FP32 collision, so
-// per node it is bound by instruction issue, not by HBM; so is the FP32 step on the Chai route,
-// whose strain rate costs more arithmetic than Yu's.  A thread here owns two x-adjacent nodes:
+// per node it is bound by instruction issue, not by HBM.  A thread here owns two x-adjacent nodes:
 // they share the pull's address arithmetic (pull2: one paired load where c_x = 0), and their
 // collisions run side by side as one pair of FP32 lanes, each add, multiply and fused multiply-add
 // acting on both lanes with one instruction (add/mul/fma.rn.f32x2; round to nearest in each lane,
@@ -16,9 +15,8 @@
 // from moments, f*_i = sum_k T_ki G_k with G_k = m*_k / |T_k|^2 (eq. (mrteqvT) with the orthogonal
 // basis: T^-1 = T^t diag(1/|T_k|^2)), instead of the one-node kernels' delta form f* = f - T^-1(...):
 // the pulled populations then die after the forward transform.  The FP32 rounding of the moment
-// form is far below the 16-bit storage's (2^-11 relative for FP16, 2^-8 for BF16), and with FP32
-// storage of the delta-rho form (populations of the size of their collision increments) it is of
-// the size of the delta form's.  Both nodes' results leave with one paired store per population.
+// form is far below the 16-bit storage's (2^-11 relative for FP16, 2^-8 for BF16), and both nodes'
+// results leave with one 32-bit store per population.
 #pragma once
 
 #include "step.cuh"
@@ -221,21 +219,7 @@ __device__ __forceinline__ void step_pair(const StepArgs<float>& a, const F2 (&f
     sfor<Q>([&](auto i) { Store<ST>::st2(static_cast<ST*>(a.dstp[CV(i)]) + node, fs[i].lo(), fs[i].hi()); });
 }
 
-// Which steps run two nodes per thread in pair arithmetic (when nx is even and the call is not a
-// read-out): every 16-bit step (Newtonian or Smagorinsky closure, the ones 16-bit storage
-// builds), and the FP32 Chai route of the 3D lattices with those closures, whose one-node kernel
-// is bound by its arithmetic rather than by HBM (the FP32 Yu route already runs at the HBM bound
-// one node per thread and keeps the delta form).
-template <class L, class ST, int CLOSURE, int FORMULA>
-__host__ __device__ constexpr bool pair_form() {
-    if constexpr (sizeof(ST) == 2)
-        return true;
-    else
-        return std::is_same<ST, float>::value && FORMULA == F_CHAI && L::D == 3 &&
-               (CLOSURE == CL_NEWTON || CLOSURE == CL_SMAG);
-}
-
-// Two x-adjacent nodes per thread (nx even).  Bound to 7 resident blocks per SM
+// Two x-adjacent nodes per thread (16-bit storage, nx even).  Bound to 7 resident blocks per SM
 // (72 registers) for both routes: measured on a GB300 against 8 blocks (Yu: channel -4%, 512^3 box
 // +1%) and, for the Chai route, 6 and 5 blocks (80 and 96 registers, fewer spilled values: channel
 // FP16 40.6 and 43.4 against 45.4 GLUPS, 512^3 box within 1%).

@@ -246,7 +246,7 @@ cudaError_t launch_stream_form(const StepArgs<typename Store<ST>::R>& a0, const 
     const long long N = (long long)a0.nx * a0.ny * a0.nz;
     if (!force_stream && N > (1LL << 23)) return cudaErrorNotSupported;
     StreamCtl u;
-    if constexpr (pair_form<L, ST, C, F>()) {
+    if constexpr (sizeof(ST) == 2) {
         if (a0.nx % 2 == 0) {
             static const int resident = resident_blocks(k_step_stream_pair<L, ST, C, F, FO>);
             if (!pick_units(c, a0.ny, a0.nz, resident, &u) && !force_stream) return cudaErrorNotSupported;
